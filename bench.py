@@ -1,0 +1,393 @@
+#!/usr/bin/env python3
+"""Benchmark: cooperative frontier SSSP on an R-MAT scale-20 graph (one GB300).
+
+Workload (the headline configuration): directed R-MAT, scale 20, edge factor 16,
+a/b/c/d = 0.57/0.19/0.19/0.05, seed 20, self-loops and duplicates removed; uint32
+weights uniform in [1, 255] (seed 21); source = highest out-degree vertex.  One step
+= one complete traversal (init kernel + persistent cooperative kernel) with the graph
+already resident in HBM.  value = GTEPS = E_s / t, E_s = out-edges of reached vertices.
+
+Also on the same JSON line: the roofline of the persistent kernel (algorithmic bytes
+4V + 24 V_r + 12 E_s per launch over its CUDA-event duration against the measured HBM
+copy bandwidth), the end-to-end number through the C ABI with host buffers (H2D of
+the CSR and weights, D2H of the distances inside the timed region), the CPU oracle
+timed on this host, clock samples taken during the timed region, and secondary
+figures: BFS on R-MAT scale 22, the 256x256 grid BFS (barrier-latency bound) and the
+non-cooperative baseline's overhead ratio.
+
+--impl reference times the CPU oracle (binary-heap Dijkstra, one core) on the same
+workload: the slow reference arm.
+
+Multi-GPU (--gpus N under torchrun): replicas only -- every rank runs the same
+workload on its own GPU; value = all ranks' edges / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BFS/SSSP GTEPS (1 GB300, % HBM roofline); barrier us; co-runner p99 latency"
+WORKLOAD = "rmat20-sssp"
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of coop_traverse<SSSP> on the
+# workload above, from the ncu capture summarised in profiles/; valid only for the
+# kernel sources with this digest (otherwise reported as null).
+TRAFFIC = {"sources_sha": None, "bytes": None}
+
+
+def sources_sha() -> str:
+    h = hashlib.sha256()
+    for rel in ("paper_1707_01989_gb300/csrc/coop.cu", "paper_1707_01989_gb300/csrc/coop_runtime.cuh"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_workload(scale=20, seed=20, wseed=21):
+    import graphgen as gg
+    g = gg.rmat(scale, 16, seed=seed)
+    w = gg.weights(g, wseed)
+    return g, w, gg.max_out_degree_vertex(g)
+
+
+def reached_work(g, reached_mask):
+    import numpy as np
+    deg = np.diff(g.row_off.astype(np.int64))
+    return int(reached_mask.sum()), int(deg[reached_mask].sum())
+
+
+def time_cpu_oracle(g, w, src, budget_s=10.0, max_runs=8):
+    """Time the oracle's Dijkstra as it stands (one core), whole traversals until budget."""
+    import oracle
+    times = []
+    t_start = time.perf_counter()
+    while len(times) < max_runs and (time.perf_counter() - t_start) < budget_s:
+        t0 = time.perf_counter()
+        d = oracle.dijkstra(g, w, src)
+        times.append(time.perf_counter() - t0)
+    return d, times
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle on the same workload (rank 0 only)."""
+    import numpy as np
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    g, w, src = load_workload()
+    import oracle
+    for _ in range(args.warmup):
+        oracle.dijkstra(g, w, src)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        d = oracle.dijkstra(g, w, src)
+        times.append(time.perf_counter() - t0)
+    _, es = reached_work(g, d != np.uint32(0xFFFFFFFF))
+    t = statistics.mean(times)
+    val = es / t / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(val, 6), "unit": "GTEPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "scale": 20, "edge_factor": 16, "V": g.num_vertices, "E": g.num_edges},
+        "cpu_baseline": {"value": round(val, 6), "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} full Dijkstra traversals of the rmat20 workload"},
+        "e2e": {"value": round(val, 6), "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the secondary workloads")
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1707_01989_gb300 as coop
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    args.warmup = max(3, args.warmup)
+
+    g, w, src = load_workload()
+    V, E = g.num_vertices, g.num_edges
+    ro_h = torch.from_numpy(np.array(g.row_off)).pin_memory()
+    col_h = torch.from_numpy(np.array(g.col)).pin_memory()
+    w_h = torch.from_numpy(w.view(np.int32)).pin_memory()
+    ro, col, wt = ro_h.to(dev), col_h.to(dev), w_h.to(dev)
+    dist_d = torch.empty(V, dtype=torch.int32, device=dev)
+    dist_h = torch.empty(V, dtype=torch.int32).pin_memory()
+    csr = coop.make_csr(ro, col)
+    ctx = coop.coop_init(local)
+    coop.coop_set_timing(ctx, True)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def step():
+        coop.coop_sssp(ctx, csr, wt, src, dist_d, stream=stream)
+
+    # correctness of what we time: one run against the oracle's invariants below
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    st = coop.coop_get_stats(ctx)
+    d = dist_d.cpu().numpy().view(np.uint32)
+    reached = d != np.uint32(0xFFFFFFFF)
+    vr, es = reached_work(g, reached)
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    step_ms, kern_us = [], []
+    with ClockSampler(local) as clocks:
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            kern_us.append(coop.coop_get_stats(ctx).kernel_us)
+    torch.cuda.synchronize(dev)
+    t_step = statistics.mean(step_ms) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_step], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+        dist.barrier()
+    value = es * world / t_step / 1e9
+
+    # roofline of the dominant kernel (the persistent traversal kernel)
+    hbm, peak_kind = peaks()
+    B = 4 * V + 24 * vr + 12 * es
+    k_s = statistics.mean(kern_us) / 1e6
+    achieved = B / k_s / 1e9
+    traffic = TRAFFIC["bytes"] if TRAFFIC["sources_sha"] == sources_sha() else None
+
+    # end to end through the C ABI with host buffers: H2D inputs, traversal, D2H result
+    h2d = (V + 1) * 4 + E * 4 + E * 4
+    d2h = V * 4
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            ro.copy_(ro_h, non_blocking=True)
+            col.copy_(col_h, non_blocking=True)
+            wt.copy_(w_h, non_blocking=True)
+        step()
+        with torch.cuda.stream(stream):
+            dist_h.copy_(dist_d, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_val = es * world / (statistics.mean(e2e_ms) / 1e3) / 1e9
+
+    extras = {}
+    cpu = None
+    if rank == 0:
+        if not args.no_extras:
+            extras = secondary(coop, ctx, dev, stream, flush, args)
+        dref, times = time_cpu_oracle(g, w, src, budget_s=args.cpu_budget)
+        parity = bool(np.array_equal(dref, d))
+        cpu = {"value": round(es / statistics.mean(times) / 1e9, 6), "unit": "GTEPS", "cores": 1, "kind": "oracle",
+               "sample": f"{len(times)} full Dijkstra traversal(s) of the rmat20 workload on 1 host core "
+                         f"({os.cpu_count()} cores present)"}
+        extras["parity_vs_oracle"] = parity
+
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(t_step * 1e3, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "scale": 20, "edge_factor": 16, "V": V, "E": E, "V_reached": vr,
+                       "E_s": es, "source": src, "weights": "uint32 U[1,255]", "parallelism": "replicas",
+                       "l2": "flushed between steps (512 MB write)", "ctas": st.max_active,
+                       "threads_per_cta": 992},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(achieved / hbm, 4), "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "coop_traverse<SSSP>", "kernel_us": round(k_s * 1e6, 2),
+                         "algorithmic_bytes": B},
+            "e2e": {"value": round(e2e_val, 4), "unit": "GTEPS", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clocks.summary(),
+            "cpu_baseline": cpu,
+            "stats": {"levels": st.levels, "barriers": st.barriers, "frontier_total": st.frontier_total,
+                      "relaxation_edges": st.edges_scanned, "work_inflation": round(st.edges_scanned / es, 3)},
+            "extras": extras,
+        }
+        print(json.dumps(line), flush=True)
+    coop.coop_destroy(ctx)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def secondary(coop, ctx, dev, stream, flush, args):
+    """BFS on R-MAT 22, grid BFS, barrier latency and the non-cooperative baseline ratio."""
+    import numpy as np
+    import torch
+    import graphgen as gg
+    out = {}
+
+    def timed(fn, reps):
+        ts, ks = [], []
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            ks.append(coop.coop_get_stats(ctx).kernel_us)
+        return statistics.median(ts), statistics.median(ks)
+
+    hbm, _ = peaks()
+    # BFS on R-MAT scale 22
+    g = gg.rmat(22, 16, seed=22)
+    src = gg.max_out_degree_vertex(g)
+    ro = torch.from_numpy(np.array(g.row_off)).to(dev)
+    col = torch.from_numpy(np.array(g.col)).to(dev)
+    lv = torch.empty(g.num_vertices, dtype=torch.int32, device=dev)
+    csr = coop.make_csr(ro, col)
+    f = lambda: coop.coop_bfs(ctx, csr, src, lv, stream=stream)
+    for _ in range(3):
+        f()
+    ms, kus = timed(f, max(3, args.steps))
+    lvh = lv.cpu().numpy()
+    vr, es = reached_work(g, lvh >= 0)
+    B = 4 * g.num_vertices + 20 * vr + 8 * es
+    fb = lambda: coop.coop_bfs_baseline(ctx, csr, src, lv, stream=stream)
+    for _ in range(2):
+        fb()
+    msb, kusb = timed(fb, max(3, args.steps))
+    out["bfs_rmat22"] = {"V": g.num_vertices, "E": g.num_edges, "E_s": es, "V_reached": vr,
+                         "ms": round(ms, 4), "kernel_us": round(kus, 2), "gteps": round(es / (ms / 1e3) / 1e9, 3),
+                         "hbm_frac": round(B / (kus / 1e6) / 1e9 / hbm, 4),
+                         "baseline_kernel_us": round(kusb, 2), "coop_overhead": round(kus / kusb, 4)}
+    del ro, col, lv
+    # grid 256x256 BFS: barrier-latency bound
+    g = gg.grid(256, 256)
+    ro = torch.from_numpy(np.array(g.row_off)).to(dev)
+    col = torch.from_numpy(np.array(g.col)).to(dev)
+    lv = torch.empty(g.num_vertices, dtype=torch.int32, device=dev)
+    csr = coop.make_csr(ro, col)
+    f = lambda: coop.coop_bfs(ctx, csr, 0, lv, stream=stream)
+    for _ in range(3):
+        f()
+    ms, kus = timed(f, max(3, args.steps))
+    ok = bool(np.array_equal(lv.cpu().numpy(), np.add(*np.divmod(np.arange(65536), 256))))
+    out["grid_bfs"] = {"levels": 511, "ms": round(ms, 4), "kernel_us": round(kus, 2),
+                       "us_per_level": round(kus / 511, 3), "closed_form_ok": ok}
+    # empty resizing barriers at M = N
+    n = 20000
+    f = lambda: coop.coop_barrier_bench(ctx, n, stream=stream, stats=False)
+    f()
+    ms, kus = timed(f, 3)
+    out["barrier_us"] = round(kus / n, 4)
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,209 @@
+/*
+ * coop.h - C ABI of libcoop.so: cooperative BFS / SSSP on one GB300 (sm_103a).
+ *
+ * Implements the cooperative-kernels programming model of Sorensen, Evrard and
+ * Donaldson, "Cooperative Kernels: GPU Multitasking for Blocking Algorithms"
+ * (FSE 2017), for its frontier graph-traversal application (Sec. 3.2, Fig. 4;
+ * Table 1's bfs and l-sssp).  A traversal runs as one persistent kernel whose CTAs
+ * (the paper's workgroups) synchronise through a resizing global barrier
+ * (Sec. 3.1; the query barrier of Sec. 4.2) and cooperate with a host-side
+ * scheduler: CTAs leave through offer_kill when the host asks for SMs
+ * (coop_request_resources) and new CTAs join through request_fork when the host
+ * returns them (coop_release).  Results do not depend on the schedule.
+ *
+ * Conventions
+ *  - Every pointer argument named d_* or inside coop_csr is DEVICE memory owned by the
+ *    caller (e.g. a torch tensor); it must stay valid until the traversal's stream
+ *    has synchronised.  Scratch (frontier queues, visited bitmap, control block) and
+ *    the host mailbox are owned by the context.
+ *  - Calls return coop_status; negative values are errors.  No call aborts or throws.
+ *  - A coop_stream is a cudaStream_t (same type, declared here without CUDA headers);
+ *    NULL is the legacy default stream.
+ *  - Graphs are int32 CSR: row_off[V+1] with row_off[0] = 0, non-decreasing,
+ *    row_off[V] = E < 2^31; col[E] with 0 <= col[e] < V.  The kernels bounds-check
+ *    every vertex id and row offset they read and report COOP_EGRAPH instead of
+ *    touching memory out of range.
+ *  - One context drives one traversal at a time.  coop_request_resources and
+ *    coop_release may be called from another host thread while a traversal runs.
+ */
+#ifndef COOP_H
+#define COOP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *coop_stream; /* == cudaStream_t */
+typedef struct coop_ctx coop_ctx;        /* opaque, library-owned */
+
+typedef enum {
+    COOP_OK = 0,
+    COOP_EINVAL = -1,    /* bad argument (null pointer, source out of range, V < 1 ...) */
+    COOP_ENOMEM = -2,    /* device or pinned host allocation failed */
+    COOP_ECUDA = -3,     /* a CUDA runtime call failed */
+    COOP_ETIMEOUT = -4,  /* a device wait or a host gather exceeded its time limit */
+    COOP_EBUSY = -5,     /* the context is busy (e.g. destroy with a traversal in flight) */
+    COOP_EOVERFLOW = -6, /* an SSSP distance did not fit below 2^32 - 1 */
+    COOP_EGRAPH = -7     /* malformed CSR detected on the device (id or offset out of range) */
+} coop_status;
+
+/* A directed graph in int32 CSR form; row_off and col are device pointers. */
+typedef struct {
+    int32_t num_vertices; /* V >= 1 */
+    int64_t num_edges;    /* E, 0 <= E < 2^31, must equal row_off[V] */
+    const int32_t *row_off;
+    const int32_t *col;
+} coop_csr;
+
+/* What one traversal did (all counters cover the whole run). */
+typedef struct {
+    int32_t levels;         /* frontier rounds expanded (BFS levels; SSSP rounds) */
+    int32_t barriers;       /* resizing barriers passed, excluding the entry one */
+    int32_t kills;          /* CTAs that left through offer_kill */
+    int32_t forks;          /* CTAs that joined through request_fork after entry */
+    int32_t min_active;     /* smallest active CTA count M seen */
+    int32_t max_active;     /* largest active CTA count M seen */
+    int32_t initial_active; /* M after the entry barrier */
+    int32_t status;         /* coop_status of the run */
+    int64_t edges_scanned;  /* sum of out-degrees over every frontier (BFS: E_s) */
+    int64_t frontier_total; /* sum of frontier sizes */
+    double gather_us_max;   /* longest coop_request_resources wait during the run */
+    double kernel_us;       /* persistent-kernel time on the launch stream (0 unless timing is on) */
+} coop_stats;
+
+/*
+ * Create a context on `device`.  max_ctas is N, the launch limit of Sec. 3.1
+ * ("a maximum of N workgroups"); 0 picks every CTA that can be co-resident (one per
+ * SM).  threads_per_cta must be 0 (default) or the compiled worker count (992).
+ * Allocates the control block and a mapped pinned mailbox.  *out = NULL on error.
+ */
+coop_status coop_init(int device, int max_ctas, int threads_per_cta, coop_ctx **out);
+
+/* Free everything the context owns.  Waits for its last traversal; NULL is a no-op. */
+coop_status coop_destroy(coop_ctx *ctx);
+
+/*
+ * Level-synchronous BFS from `source` (Sec. 2.2 Fig. 3 made cooperative as in Sec. 3.2
+ * Fig. 4; Table 1 "bfs").  Writes d_levels[v] = fewest edges on a path source -> v,
+ * -1 if unreachable (int32[V], device).  Asynchronous on `stream` unless stats is
+ * non-NULL, in which case it waits for the traversal and fills *stats.
+ */
+coop_status coop_bfs(coop_ctx *ctx, const coop_csr *g, int32_t source, int32_t *d_levels,
+                     coop_stream stream, coop_stats *stats);
+
+/*
+ * Frontier single-source shortest paths (Table 1 "l-sssp", read as data-driven
+ * Bellman-Ford): d_dist[v] = least total weight of a path source -> v, 0xFFFFFFFF if
+ * unreachable (uint32[V], device); d_weights is uint32[E] (device).  Every shortest
+ * distance must fit below 2^32 - 1, else the run reports COOP_EOVERFLOW.
+ * Asynchronous unless stats is non-NULL (as coop_bfs).
+ */
+coop_status coop_sssp(coop_ctx *ctx, const coop_csr *g, const uint32_t *d_weights,
+                      int32_t source, uint32_t *d_dist, coop_stream stream, coop_stats *stats);
+
+/*
+ * The scheduler asks the running cooperative kernel for n_ctas CTAs (Sec. 4.2,
+ * "Launching Kernels and Managing Workgroups": command K_c to provide N - N_a
+ * workgroups via offer_kill).  Blocks until the CTAs have left (or, with no traversal
+ * in flight, grants them at once), at most timeout_us microseconds (<= 0: no limit).
+ * *n_freed (nullable) receives how many left.  On COOP_ETIMEOUT the request stays
+ * pending; CTAs it frees later are also lent to the caller.  CTA 0 is never
+ * surrendered, so at most N-1 CTAs can be lent at a time (else COOP_EINVAL).
+ */
+coop_status coop_request_resources(coop_ctx *ctx, int n_ctas, int timeout_us, int *n_freed);
+
+/*
+ * Return n_ctas lent CTAs (Sec. 4.2: the scheduler signals that extra workgroups
+ * should join at the next request_fork).  If a traversal is running, n_ctas new CTAs
+ * are launched on the context's join stream; they join at the next resizing barrier
+ * with the transmitted state of the running interval.  Otherwise the next traversal
+ * simply starts with them.  COOP_EINVAL if more than are lent.
+ */
+coop_status coop_release(coop_ctx *ctx, int n_ctas);
+
+/* Wait for the last traversal (both streams) and return its status (sticky device error). */
+coop_status coop_sync(coop_ctx *ctx);
+
+/* Statistics of the last completed traversal (call after it has finished). */
+coop_status coop_get_stats(coop_ctx *ctx, coop_stats *stats);
+
+/*
+ * Resize log of the last completed traversal: one record per resizing barrier that
+ * changed M, four int32 each {M_before, k_forked, W_killed, M_after}, in order.
+ * Writes min(cap, available) records to out (host memory) and the number written to *n.
+ */
+coop_status coop_get_resize_log(coop_ctx *ctx, int32_t *out, int cap, int *n);
+
+/*
+ * Forced random schedule (tests and the multitasking benchmark).  At every resizing
+ * barrier, with probability p_kill the scheduler accepts W in [0, M-1] offer_kills,
+ * and with probability p_fork it grants up to k in [0, N-M] forks (taken from CTAs
+ * waiting to join).  reserve_ctas extra CTAs are launched with each traversal on the
+ * join stream; they occupy SMs that killed CTAs free and wait there to be forked.
+ * p_kill = p_fork = 0 disables the schedule (the default).  Draws are SplitMix64
+ * hashes of (seed, barrier index).
+ */
+coop_status coop_set_schedule(coop_ctx *ctx, uint64_t seed, double p_kill, double p_fork,
+                              int reserve_ctas);
+
+/* Time limit for every device-side wait (default 2 s).  Exceeding it ends the run with COOP_ETIMEOUT. */
+coop_status coop_set_timeout(coop_ctx *ctx, int64_t timeout_us);
+
+/*
+ * Kernel timing: when on, every traversal records CUDA events around its persistent
+ * kernel on the launch stream and coop_stats.kernel_us reports the elapsed time.
+ */
+coop_status coop_set_timing(coop_ctx *ctx, int on);
+
+/* Context facts: N, worker threads per CTA, SM count, CTAs currently lent to the host. */
+coop_status coop_query(coop_ctx *ctx, int *max_ctas, int *threads_per_cta, int *sm_count,
+                       int *lent);
+
+/*
+ * Non-cooperative baselines (Sec. 2.2 Fig. 3): the same traversal with a plain global
+ * barrier, a fixed set of N CTAs and no scheduler interaction.  Used to measure the
+ * overhead of the cooperative primitives when nothing is resized (Sec. 5.3, Table 2).
+ */
+coop_status coop_bfs_baseline(coop_ctx *ctx, const coop_csr *g, int32_t source, int32_t *d_levels,
+                              coop_stream stream, coop_stats *stats);
+coop_status coop_sssp_baseline(coop_ctx *ctx, const coop_csr *g, const uint32_t *d_weights,
+                               int32_t source, uint32_t *d_dist, coop_stream stream,
+                               coop_stats *stats);
+
+/*
+ * Barrier benchmark / self-test: the persistent kernel with empty intervals passes
+ * n_barriers resizing barriers (schedule and host requests apply as usual).  With
+ * never_arrive > 0 the barrier waits for that many extra arrivals that never come, so
+ * the run must end with COOP_ETIMEOUT after the context's time limit (the way the
+ * failure path is tested without faulting or hanging the GPU).  Synchronous when
+ * stats is non-NULL.
+ */
+coop_status coop_barrier_bench(coop_ctx *ctx, int32_t n_barriers, int32_t never_arrive,
+                               coop_stream stream, coop_stats *stats);
+
+/*
+ * The co-running latency-critical task: y[i] = a * x[i] + y[i] for i < n (fp32,
+ * device pointers), on n_ctas CTAs whose shared-memory reservation keeps them off any
+ * SM that holds a traversal CTA, so they run only on SMs the traversal gave up (the
+ * compute stand-in for the paper's graphics / matrix-multiplication tasks, Sec. 5.4).
+ */
+coop_status coop_saxpy(int n_ctas, int64_t n, float a, const float *d_x, float *d_y,
+                       coop_stream stream);
+
+/*
+ * Text of the last failing CUDA runtime call made by this library on the calling
+ * thread ("" if none): which step failed, the CUDA error name and its description.
+ * Useful after COOP_ECUDA; the string stays valid until the thread's next failure.
+ */
+const char *coop_last_cuda_error(void);
+
+/* Human-readable name of a status code (static string). */
+const char *coop_status_string(coop_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COOP_H */

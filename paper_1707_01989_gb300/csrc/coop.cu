@@ -1,0 +1,826 @@
+// coop.cu - cooperative BFS / SSSP kernels for GB300 (sm_103a) and the C ABI of libcoop.so.
+//
+// One traversal = one init kernel + one persistent kernel (+ fork launches on the
+// context's join stream).  Inside the persistent kernel each interval between two
+// resizing barriers expands one frontier (Fig. 4 of "Cooperative Kernels", Sec. 3.2):
+//
+//  * the frontier lives in a queue of (first column, edge-space offset[, vertex]) entries;
+//    the offsets are the exclusive prefix sums of the frontier's out-degrees, built on
+//    the fly by the warp-aggregated enqueue (one 64-bit atomic per warp adds both the
+//    vertex count and the edge count);
+//  * the interval's edge space [0, edges) is split evenly over the M * 32 worker warps of
+//    the active CTAs by logical id -- the paper's tid / stride re-partition, recomputed
+//    after every resizing barrier, applied to edges instead of vertices so that skewed
+//    degrees (R-MAT hubs) are balanced;
+//  * a warp walks its edge range 32 consecutive edges at a time: a window of 32 frontier
+//    entries sits in registers, a ballot finds the entries that ended, one __reduce_or
+//    marks the entries that start inside the chunk, and a popc over lanemask_le gives
+//    each lane its source entry, so column loads are coalesced;
+//  * BFS claims a vertex with an atomicOr on a 1-bit-per-vertex visited bitmap (checked
+//    first with a plain load; stale reads only cost an extra atomic), writes its level
+//    and enqueues it if its out-degree is non-zero; SSSP relaxes with atomicMin and
+//    enqueues a lowered vertex once per round through a round stamp.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <mutex>
+#include <thread>
+
+#include "../../include/coop.h"
+#include "coop_runtime.cuh"
+
+using namespace coopdev;
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+struct Window {
+  uint32_t off, end, start, u, du;
+};
+
+// entry i of the input queue (or an empty marker past its end)
+template <int MODE>
+__device__ __forceinline__ void load_entry(const Params &p, const uint32_t *qo, const uint32_t *qs,
+                                           const uint32_t *qv, uint32_t F, uint32_t Etot, uint32_t i,
+                                           Window &w) {
+  if (i < F) {
+    w.off = qo[i];
+    w.start = qs[i];
+    w.end = (i + 1u < F) ? qo[i + 1u] : Etot;
+    if (MODE == MODE_SSSP) {
+      w.u = qv[i];
+      w.du = *(volatile const uint32_t *)(p.dist + w.u);
+    }
+  } else {
+    w.off = 0xFFFFFFFFu;
+    w.end = 0xFFFFFFFFu;
+    w.start = 0u;
+    w.u = 0u;
+    w.du = 0u;
+  }
+}
+
+// Largest i in [0, F) with qo[i] <= x (qo strictly increasing, qo[0] = 0): a 32-ary search.
+__device__ __forceinline__ uint32_t find_entry(const uint32_t *qo, uint32_t F, uint32_t x, unsigned lane) {
+  uint32_t lo = 0u, hi = F;
+  while (hi - lo > 32u) {
+    const uint32_t step = (hi - lo + 31u) / 32u;
+    const uint32_t idx = lo + lane * step;
+    const bool pred = idx < hi && qo[idx] <= x;
+    const unsigned b = __ballot_sync(kFull, pred);
+    const uint32_t L = 31u - (uint32_t)__clz(b);
+    const uint32_t nlo = lo + L * step;
+    hi = min(nlo + step, hi);
+    lo = nlo;
+  }
+  const uint32_t idx = lo + lane;
+  const bool pred = idx < hi && qo[idx] <= x;
+  const unsigned b = __ballot_sync(kFull, pred);
+  return lo + 31u - (uint32_t)__clz(b);
+}
+
+// Warp-aggregated enqueue of (v, first column, degree) for the lanes with push = true.
+__device__ __forceinline__ void enqueue(const Params &p, uint32_t out, bool push, uint32_t v, uint32_t rs,
+                                        uint32_t deg, unsigned lane) {
+  const unsigned pm = __ballot_sync(kFull, push);
+  if (pm == 0u) return;
+  uint32_t x = push ? deg : 0u;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, x, o);
+    if ((int)lane >= o) x += y;
+  }
+  const uint32_t total = __shfl_sync(kFull, x, 31);
+  unsigned long long base = 0ull;
+  if (lane == 0)
+    base = atomicAdd(&p.ctl->qctr[out], ((unsigned long long)__popc(pm) << 32) | (unsigned long long)total);
+  base = __shfl_sync(kFull, base, 0);
+  if (push) {
+    const uint32_t slot = (uint32_t)(base >> 32) + (uint32_t)__popc(pm & lanemask_lt());
+    const uint32_t off = (uint32_t)base + x - deg;
+    (out ? p.qo[1] : p.qo[0])[slot] = off;
+    (out ? p.qs[1] : p.qs[0])[slot] = rs;
+    (out ? p.qv[1] : p.qv[0])[slot] = v;
+  }
+}
+
+// Read row_off[v], row_off[v+1] of a vertex about to be enqueued; false if malformed.
+__device__ __forceinline__ bool row_of(const Params &p, uint32_t v, uint32_t &rs, uint32_t &deg) {
+  const int32_t a = __ldg(p.row_off + v), b = __ldg(p.row_off + v + 1);
+  if (a < 0 || b < a || (uint32_t)b > p.E) return false;
+  rs = (uint32_t)a;
+  deg = (uint32_t)(b - a);
+  return true;
+}
+
+// Expand this warp's share of the interval's edge space.
+template <int MODE>
+__device__ void expand(const Params &p, const Interval &iv, int32_t id) {
+  const unsigned lane = threadIdx.x & 31u;
+  const uint64_t GW = (uint64_t)iv.M * kWarps;
+  const uint64_t gw = (uint64_t)id * kWarps + (threadIdx.x >> 5);
+  const uint32_t Etot = iv.edges;
+  const uint32_t E0 = (uint32_t)((uint64_t)Etot * gw / GW);
+  const uint32_t E1 = (uint32_t)((uint64_t)Etot * (gw + 1u) / GW);
+  if (E0 >= E1) return;
+  const uint32_t F = iv.count;
+  const uint32_t in = iv.sel, out = in ^ 1u;
+  const uint32_t *qo = in ? p.qo[1] : p.qo[0];
+  const uint32_t *qs = in ? p.qs[1] : p.qs[0];
+  const uint32_t *qv = in ? p.qv[1] : p.qv[0];
+  const unsigned lm_le = lanemask_le();
+  const uint32_t next_level = (uint32_t)iv.level + 1u;
+  const uint32_t V = (uint32_t)p.V;
+
+  uint32_t wb = find_entry(qo, F, E0, lane);
+  Window w;
+  load_entry<MODE>(p, qo, qs, qv, F, Etot, wb + lane, w);
+  bool bad = false;
+  bool ovf = false;
+
+  for (uint32_t c = E0; c < E1; c += 32u) {
+    // slide the window so that lane 0 holds the entry containing edge c
+    const unsigned ended = __ballot_sync(kFull, w.end <= c);
+    if (ended) {
+      const unsigned n = (unsigned)__popc(ended);
+      wb += n;
+      const unsigned srcl = (lane + n) & 31u;
+      Window s;
+      s.off = __shfl_sync(kFull, w.off, srcl);
+      s.end = __shfl_sync(kFull, w.end, srcl);
+      s.start = __shfl_sync(kFull, w.start, srcl);
+      if (MODE == MODE_SSSP) {
+        s.u = __shfl_sync(kFull, w.u, srcl);
+        s.du = __shfl_sync(kFull, w.du, srcl);
+      }
+      if (lane + n < 32u) w = s;
+      else load_entry<MODE>(p, qo, qs, qv, F, Etot, wb + lane, w);
+    }
+    // entries starting strictly inside [c, c+32) -> source entry of each lane's edge
+    const uint32_t rel = w.off - c;
+    const unsigned bit = (lane != 0u && rel < 32u) ? (1u << rel) : 0u;
+    const unsigned bits = __reduce_or_sync(kFull, bit);
+    const unsigned idx = (unsigned)__popc(bits & lm_le);
+    const uint32_t s0 = __shfl_sync(kFull, w.start, idx);
+    const uint32_t o0 = __shfl_sync(kFull, w.off, idx);
+    uint32_t du = 0u;
+    if (MODE == MODE_SSSP) du = __shfl_sync(kFull, w.du, idx);
+    const uint32_t e = c + lane;
+    const bool valid = e < E1;
+    const uint32_t pos = s0 + (e - o0);
+
+    bool push = false;
+    uint32_t v = 0u, rs = 0u, deg = 0u;
+    if (valid) {
+      v = (uint32_t)__ldg(p.col + pos);
+      if (v >= V) {
+        bad = true;
+      } else if (MODE == MODE_BFS) {
+        const uint32_t m = 1u << (v & 31u);
+        uint32_t *word = p.visited + (v >> 5);
+        if ((*word & m) == 0u && (atomicOr(word, m) & m) == 0u) {
+          p.level[v] = (int32_t)next_level;
+          if (row_of(p, v, rs, deg)) push = deg > 0u;
+          else bad = true;
+        }
+      } else {
+        const uint64_t nd64 = (uint64_t)du + (uint64_t)__ldg(p.w + pos);
+        if (nd64 >= 0xFFFFFFFFull) {
+          ovf = true;
+        } else {
+          const uint32_t nd = (uint32_t)nd64;
+          uint32_t *dv = p.dist + v;
+          if (nd < *(volatile uint32_t *)dv && nd < atomicMin(dv, nd)) {
+            const uint32_t tag = next_level + 1u;  // stamp of "queued for the next round"
+            uint32_t *sv = p.stamp + v;
+            if (*(volatile uint32_t *)sv != tag && atomicExch(sv, tag) != tag) {
+              if (row_of(p, v, rs, deg)) push = deg > 0u;
+              else bad = true;
+            }
+          }
+        }
+      }
+    }
+    enqueue(p, out, push, v, rs, deg, lane);
+  }
+  if (bad) raise_err(p, ERR_GRAPH);
+  if (ovf) p.ctl->ovf = 1u;
+}
+
+template <int MODE>
+__device__ __forceinline__ void worker_loop(const Params &p, CtaShared &cs) {
+  for (;;) {
+    const Interval iv = cs.iv;
+    const int32_t id = cs.id;
+    if (iv.done || id >= iv.M) return;  // finished, or left through offer_kill
+    if (MODE != MODE_BARRIER) expand<MODE>(p, iv, id);
+    if (!resizing_barrier<MODE>(p, cs)) return;
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kBlock, 1) coop_traverse(const __grid_constant__ Params p, int join) {
+  __shared__ CtaShared cs;
+  if (threadIdx.x == 0) {
+    bool active;
+    if (!join && blockIdx.x == 0) {
+      master_enter<MODE>(p, cs);
+      active = true;
+    } else if (p.coop) {
+      active = join_enter(p, cs);
+    } else {
+      active = plain_enter(p, cs);
+    }
+    cs.exit = active ? 0 : 1;
+    cs.workers_left = 0;
+  }
+  __syncthreads();
+  if (cs.exit) return;
+  if (threadIdx.x >= kWorkers) {
+    if (p.coop && cs.id == 0 && threadIdx.x == kWorkers) poller(p, &cs.workers_left);
+    return;
+  }
+  worker_loop<MODE>(p, cs);
+  if (threadIdx.x == 0) *(volatile int32_t *)&cs.workers_left = 1;
+}
+
+// Per-run initialisation: outputs, scratch and the control block.
+template <int MODE>
+__global__ void __launch_bounds__(512) coop_init_kernel(const __grid_constant__ Params p) {
+  const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t nth = (size_t)gridDim.x * blockDim.x;
+  const size_t V = (size_t)(p.V > 0 ? p.V : 0);
+  if (MODE == MODE_BFS) {
+    for (size_t i = tid; i < V; i += nth) p.level[i] = -1;
+    for (size_t i = tid; i < (V + 31) / 32; i += nth) p.visited[i] = 0u;
+  } else if (MODE == MODE_SSSP) {
+    for (size_t i = tid; i < V; i += nth) {
+      p.dist[i] = 0xFFFFFFFFu;
+      p.stamp[i] = 0u;
+    }
+  }
+  // zero the control block except its header line, which thread 0 writes
+  uint32_t *cw = reinterpret_cast<uint32_t *>(p.ctl);
+  const size_t hdr = offsetof(Ctl, run) / 4, hdr_end = hdr + 32;
+  for (size_t i = tid; i < sizeof(Ctl) / 4; i += nth)
+    if (i < hdr || i >= hdr_end) cw[i] = 0u;
+  if (tid == 0) {
+    p.ctl->run = p.run;
+    p.ctl->kill_req_mirror = p.kill_base;
+    p.ctl->err = 0u;
+    p.ctl->done = 0u;
+    p.ctl->ovf = 0u;
+  }
+}
+
+// The co-running task: y = a*x + y, grid-stride, vectorised where aligned.
+__global__ void __launch_bounds__(1024) coop_saxpy_kernel(int64_t n, float a, const float *__restrict__ x,
+                                                        float *__restrict__ y) {
+  extern __shared__ uint4 reserve[];  // SM-exclusivity reservation only
+  (void)reserve;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  const bool vec = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15u) == 0u;
+  int64_t done = 0;
+  if (vec) {
+    const int64_t n4 = n / 4;
+    const float4 *x4 = reinterpret_cast<const float4 *>(x);
+    float4 *y4 = reinterpret_cast<float4 *>(y);
+    for (int64_t i = tid; i < n4; i += nth) {
+      const float4 xv = __ldg(x4 + i);
+      float4 yv = y4[i];
+      yv.x = fmaf(a, xv.x, yv.x);
+      yv.y = fmaf(a, xv.y, yv.y);
+      yv.z = fmaf(a, xv.z, yv.z);
+      yv.w = fmaf(a, xv.w, yv.w);
+      y4[i] = yv;
+    }
+    done = n4 * 4;
+  }
+  for (int64_t i = done + tid; i < n; i += nth) y[i] = fmaf(a, x[i], y[i]);
+}
+
+}  // namespace
+
+// ===================================================================== host side
+
+struct coop_ctx {
+  int device = 0;
+  int N = 0;
+  int sm_count = 0;
+  cudaStream_t join_stream = nullptr;
+  cudaEvent_t ev_init = nullptr, ev_done = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;  // kernel timing (optional)
+  bool timing = false;
+  Mailbox *mbox = nullptr;    // host view
+  Mailbox *mbox_d = nullptr;  // device view of the same pinned page
+  Ctl *ctl = nullptr;
+  void *scratch = nullptr;
+  int64_t cap_V = 0;
+  uint32_t *visited = nullptr, *stamp = nullptr;
+  uint32_t *qv[2] = {nullptr, nullptr}, *qs[2] = {nullptr, nullptr}, *qo[2] = {nullptr, nullptr};
+  std::mutex mu;
+  uint32_t run = 0;
+  bool launched = false;
+  Params cur{};
+  int cur_mode = MODE_BFS;
+  uint32_t kill_req = 0, served = 0, returned = 0;
+  int64_t timeout_us = 2000000;
+  uint64_t sched_seed = 0;
+  double p_kill = 0.0, p_fork = 0.0;
+  int reserve = 0;
+  double gather_us_max = 0.0;
+};
+
+namespace {
+
+thread_local char g_last_error[256] = "";
+
+// Record a failing CUDA call (what + the runtime's error name and string) for
+// coop_last_cuda_error(); returns true when `e` is an error.
+bool cuda_failed(cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return false;
+  snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+  (void)cudaGetLastError();
+  return true;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int now = -1;
+    if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+  }
+};
+
+inline uint32_t load_acquire(const uint32_t *p) { return __atomic_load_n(p, __ATOMIC_ACQUIRE); }
+inline void store_release(uint32_t *p, uint32_t v) { __atomic_store_n(p, v, __ATOMIC_RELEASE); }
+
+bool running(coop_ctx *c) { return c->launched && cudaEventQuery(c->ev_done) == cudaErrorNotReady; }
+
+// Fold a finished run's kills into the host's books and grant outstanding requests.
+void finalize_locked(coop_ctx *c) {
+  if (running(c)) return;
+  (void)cudaGetLastError();
+  const uint32_t f = load_acquire(&c->mbox->freed);
+  if ((int32_t)(f - c->served) > 0) c->served = f;
+  if ((int32_t)(c->kill_req - c->served) > 0) c->served = c->kill_req;  // idle grant
+  store_release(&c->mbox->freed, c->served);
+}
+
+coop_status ensure_scratch(coop_ctx *c, int64_t V) {
+  if (V <= c->cap_V) return COOP_OK;
+  if (c->scratch) {
+    cudaStreamSynchronize(c->join_stream);
+    cudaFree(c->scratch);
+    c->scratch = nullptr;
+    c->cap_V = 0;
+  }
+  const int64_t cap = std::max<int64_t>(V, 1024);
+  const size_t words = (size_t)(cap + 31) / 32;
+  const size_t qbytes = (size_t)cap * 4;
+  const size_t total = words * 4 + qbytes * 7 + 7 * 256;
+  char *base = nullptr;
+  if (cudaMalloc(&base, total) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return COOP_ENOMEM;
+  }
+  size_t at = 0;
+  auto take = [&](size_t b) {
+    char *p = base + at;
+    at += (b + 255) & ~(size_t)255;
+    return reinterpret_cast<uint32_t *>(p);
+  };
+  c->visited = take(words * 4);
+  c->stamp = take(qbytes);
+  for (int i = 0; i < 2; ++i) {
+    c->qv[i] = take(qbytes);
+    c->qs[i] = take(qbytes);
+    c->qo[i] = take(qbytes);
+  }
+  c->scratch = base;
+  c->cap_V = cap;
+  return COOP_OK;
+}
+
+coop_status check_graph(const coop_csr *g, int32_t source) {
+  if (!g || !g->row_off || g->num_vertices < 1) return COOP_EINVAL;
+  if (g->num_edges < 0 || g->num_edges >= ((int64_t)1 << 31)) return COOP_EINVAL;
+  if (g->num_edges > 0 && !g->col) return COOP_EINVAL;
+  if (source < 0 || source >= g->num_vertices) return COOP_EINVAL;
+  return COOP_OK;
+}
+
+template <int MODE>
+coop_status launch_run(coop_ctx *c, const coop_csr *g, const uint32_t *w, int32_t source, int32_t *level,
+                       uint32_t *dist, cudaStream_t stream, coop_stats *stats, bool coop, int32_t n_barriers,
+                       int32_t extra_wait) {
+  DeviceGuard guard(c->device);
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (c->launched && running(c)) cudaEventSynchronize(c->ev_done);  // one traversal at a time
+    finalize_locked(c);
+    const int64_t V = g ? g->num_vertices : 0;
+    coop_status st = ensure_scratch(c, std::max<int64_t>(V, 1));
+    if (st != COOP_OK) return st;
+    const int held = (int)(c->served - c->returned);
+    const int launched = coop ? std::max(1, c->N - held) : c->N;
+    Params p{};
+    if (g) {
+      p.row_off = g->row_off;
+      p.col = g->col;
+      p.V = g->num_vertices;
+      p.E = (uint32_t)g->num_edges;
+    }
+    p.w = w;
+    p.level = level;
+    p.dist = dist;
+    p.visited = c->visited;
+    p.stamp = c->stamp;
+    for (int i = 0; i < 2; ++i) {
+      p.qv[i] = c->qv[i];
+      p.qs[i] = c->qs[i];
+      p.qo[i] = c->qo[i];
+    }
+    p.ctl = c->ctl;
+    p.mbox = c->mbox_d;
+    p.src = source;
+    p.N = c->N;
+    p.launched = (uint32_t)launched;
+    p.kill_base = c->served;
+    p.timeout_ns = (uint64_t)std::max<int64_t>(c->timeout_us, 1) * 1000ull;
+    p.sched_seed = c->sched_seed;
+    p.p_kill = (uint32_t)std::min(4294967295.0, std::max(0.0, c->p_kill) * 4294967296.0);
+    p.p_fork = (uint32_t)std::min(4294967295.0, std::max(0.0, c->p_fork) * 4294967296.0);
+    p.sched_on = (coop && (c->p_kill > 0.0 || c->p_fork > 0.0)) ? 1u : 0u;
+    p.run = ++c->run;
+    p.n_barriers = n_barriers;
+    p.extra_wait = (uint32_t)std::max(0, extra_wait);
+    p.coop = coop ? 1u : 0u;
+
+    c->mbox->err = 0;
+    c->mbox->status = 0;
+    store_release(&c->mbox->freed, c->served);
+    store_release(&c->mbox->kill_req, c->kill_req);
+
+    cudaStreamWaitEvent(stream, c->ev_join, 0);  // fork launches of earlier runs are gone
+    coop_init_kernel<MODE><<<c->sm_count * 4, 512, 0, stream>>>(p);
+    cudaEventRecord(c->ev_init, stream);
+    if (c->timing) cudaEventRecord(c->ev_t0, stream);
+    coop_traverse<MODE><<<launched, kBlock, kReserveSmem, stream>>>(p, 0);
+    if (c->timing) cudaEventRecord(c->ev_t1, stream);
+    if (coop && p.sched_on && c->reserve > 0) {
+      cudaStreamWaitEvent(c->join_stream, c->ev_init, 0);
+      coop_traverse<MODE><<<c->reserve, kBlock, kReserveSmem, c->join_stream>>>(p, 1);
+    }
+    cudaEventRecord(c->ev_join, c->join_stream);
+    cudaEventRecord(c->ev_done, stream);
+    if (cuda_failed(cudaGetLastError(), "traversal launch")) return COOP_ECUDA;
+    c->cur = p;
+    c->cur_mode = MODE;
+    c->launched = true;
+    c->gather_us_max = 0.0;
+  }
+  if (stats) {
+    if (cudaEventSynchronize(c->ev_done) != cudaSuccess) return COOP_ECUDA;
+    return coop_get_stats(c, stats);
+  }
+  return COOP_OK;
+}
+
+template <int MODE>
+void launch_join(coop_ctx *c, int n) {
+  coop_traverse<MODE><<<n, kBlock, kReserveSmem, c->join_stream>>>(c->cur, 1);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *coop_last_cuda_error(void) { return g_last_error; }
+
+const char *coop_status_string(coop_status s) {
+  switch (s) {
+    case COOP_OK: return "COOP_OK";
+    case COOP_EINVAL: return "COOP_EINVAL";
+    case COOP_ENOMEM: return "COOP_ENOMEM";
+    case COOP_ECUDA: return "COOP_ECUDA";
+    case COOP_ETIMEOUT: return "COOP_ETIMEOUT";
+    case COOP_EBUSY: return "COOP_EBUSY";
+    case COOP_EOVERFLOW: return "COOP_EOVERFLOW";
+    case COOP_EGRAPH: return "COOP_EGRAPH";
+  }
+  return "COOP_UNKNOWN";
+}
+
+coop_status coop_init(int device, int max_ctas, int threads_per_cta, coop_ctx **out) {
+  if (!out) return COOP_EINVAL;
+  *out = nullptr;
+  if (max_ctas < 0 || (threads_per_cta != 0 && threads_per_cta != kWorkers)) return COOP_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    (void)cudaGetLastError();
+    return COOP_EINVAL;
+  }
+  DeviceGuard guard(device);
+  coop_ctx *c = new coop_ctx();
+  c->device = device;
+  auto fail = [&](coop_status s) {
+    coop_destroy(c);
+    (void)cudaGetLastError();
+    return s;
+  };
+  if (cuda_failed(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device), "sm count"))
+    return fail(COOP_ECUDA);
+  const void *kernels[] = {(const void *)coop_traverse<MODE_BFS>, (const void *)coop_traverse<MODE_SSSP>,
+                           (const void *)coop_traverse<MODE_BARRIER>};
+  int per_sm = 1 << 30;
+  for (const void *k : kernels) {
+    if (cuda_failed(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kReserveSmem),
+                    "set traversal smem"))
+      return fail(COOP_ECUDA);
+    int nb = 0;
+    if (cuda_failed(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBlock, kReserveSmem), "occupancy"))
+      return fail(COOP_ECUDA);
+    per_sm = std::min(per_sm, nb);
+  }
+  if (cuda_failed(cudaFuncSetAttribute((const void *)coop_saxpy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kCorunnerSmem),
+                  "set co-runner smem"))
+    return fail(COOP_ECUDA);
+  if (per_sm < 1) {
+    snprintf(g_last_error, sizeof(g_last_error), "traversal kernel cannot be resident (%d per SM)", per_sm);
+    return fail(COOP_ECUDA);
+  }
+  const int cap = std::min(per_sm * c->sm_count, kMaxCtas);
+  c->N = max_ctas == 0 ? cap : std::min(max_ctas, cap);
+  if (cuda_failed(cudaStreamCreateWithFlags(&c->join_stream, cudaStreamNonBlocking), "join stream"))
+    return fail(COOP_ECUDA);
+  if (cuda_failed(cudaEventCreateWithFlags(&c->ev_init, cudaEventDisableTiming), "event") ||
+      cuda_failed(cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming), "event") ||
+      cuda_failed(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "event"))
+    return fail(COOP_ECUDA);
+  if (cuda_failed(cudaHostAlloc((void **)&c->mbox, sizeof(Mailbox), cudaHostAllocMapped | cudaHostAllocPortable),
+                  "mailbox"))
+    return fail(COOP_ENOMEM);
+  memset(c->mbox, 0, sizeof(Mailbox));
+  if (cuda_failed(cudaHostGetDevicePointer((void **)&c->mbox_d, c->mbox, 0), "mailbox device pointer"))
+    return fail(COOP_ECUDA);
+  if (cuda_failed(cudaMalloc((void **)&c->ctl, sizeof(Ctl)), "control block")) return fail(COOP_ENOMEM);
+  if (cuda_failed(cudaMemset(c->ctl, 0, sizeof(Ctl)), "control block memset")) return fail(COOP_ECUDA);
+  cudaEventRecord(c->ev_join, c->join_stream);
+  if (cuda_failed(cudaDeviceSynchronize(), "init sync")) return fail(COOP_ECUDA);
+  *out = c;
+  return COOP_OK;
+}
+
+coop_status coop_destroy(coop_ctx *c) {
+  if (!c) return COOP_OK;
+  DeviceGuard guard(c->device);
+  if (c->ev_done && c->launched) cudaEventSynchronize(c->ev_done);
+  if (c->join_stream) cudaStreamSynchronize(c->join_stream);
+  if (c->scratch) cudaFree(c->scratch);
+  if (c->ctl) cudaFree(c->ctl);
+  if (c->mbox) cudaFreeHost(c->mbox);
+  if (c->ev_init) cudaEventDestroy(c->ev_init);
+  if (c->ev_done) cudaEventDestroy(c->ev_done);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_t0) cudaEventDestroy(c->ev_t0);
+  if (c->ev_t1) cudaEventDestroy(c->ev_t1);
+  if (c->join_stream) cudaStreamDestroy(c->join_stream);
+  (void)cudaGetLastError();
+  delete c;
+  return COOP_OK;
+}
+
+coop_status coop_bfs(coop_ctx *c, const coop_csr *g, int32_t source, int32_t *d_levels, coop_stream stream,
+                     coop_stats *stats) {
+  if (!c || !d_levels) return COOP_EINVAL;
+  const coop_status st = check_graph(g, source);
+  if (st != COOP_OK) return st;
+  return launch_run<MODE_BFS>(c, g, nullptr, source, d_levels, nullptr, (cudaStream_t)stream, stats, true, 0, 0);
+}
+
+coop_status coop_sssp(coop_ctx *c, const coop_csr *g, const uint32_t *d_weights, int32_t source, uint32_t *d_dist,
+                      coop_stream stream, coop_stats *stats) {
+  if (!c || !d_dist) return COOP_EINVAL;
+  const coop_status st = check_graph(g, source);
+  if (st != COOP_OK) return st;
+  if (g->num_edges > 0 && !d_weights) return COOP_EINVAL;
+  return launch_run<MODE_SSSP>(c, g, d_weights, source, nullptr, d_dist, (cudaStream_t)stream, stats, true, 0, 0);
+}
+
+coop_status coop_bfs_baseline(coop_ctx *c, const coop_csr *g, int32_t source, int32_t *d_levels,
+                              coop_stream stream, coop_stats *stats) {
+  if (!c || !d_levels) return COOP_EINVAL;
+  const coop_status st = check_graph(g, source);
+  if (st != COOP_OK) return st;
+  return launch_run<MODE_BFS>(c, g, nullptr, source, d_levels, nullptr, (cudaStream_t)stream, stats, false, 0, 0);
+}
+
+coop_status coop_sssp_baseline(coop_ctx *c, const coop_csr *g, const uint32_t *d_weights, int32_t source,
+                               uint32_t *d_dist, coop_stream stream, coop_stats *stats) {
+  if (!c || !d_dist) return COOP_EINVAL;
+  const coop_status st = check_graph(g, source);
+  if (st != COOP_OK) return st;
+  if (g->num_edges > 0 && !d_weights) return COOP_EINVAL;
+  return launch_run<MODE_SSSP>(c, g, d_weights, source, nullptr, d_dist, (cudaStream_t)stream, stats, false, 0,
+                               0);
+}
+
+coop_status coop_barrier_bench(coop_ctx *c, int32_t n_barriers, int32_t never_arrive, coop_stream stream,
+                               coop_stats *stats) {
+  if (!c || n_barriers < 0 || never_arrive < 0) return COOP_EINVAL;
+  return launch_run<MODE_BARRIER>(c, nullptr, nullptr, 0, nullptr, nullptr, (cudaStream_t)stream, stats, true,
+                                  n_barriers, never_arrive);
+}
+
+coop_status coop_request_resources(coop_ctx *c, int n, int timeout_us, int *n_freed) {
+  if (n_freed) *n_freed = 0;
+  if (!c || n < 1) return COOP_EINVAL;
+  uint32_t target;
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    finalize_locked(c);
+    const int outstanding = (int)(c->kill_req - c->returned);
+    if (outstanding + n > c->N - 1) return COOP_EINVAL;
+    c->kill_req += (uint32_t)n;
+    target = c->kill_req;
+    store_release(&c->mbox->kill_req, c->kill_req);
+    if (!running(c)) {
+      finalize_locked(c);
+      if (n_freed) *n_freed = n;
+      return COOP_OK;
+    }
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  for (uint32_t spin = 0;; ++spin) {
+    const uint32_t f = load_acquire(&c->mbox->freed);
+    const int got = std::max(0, std::min(n, (int)(f - (target - (uint32_t)n))));
+    if ((int32_t)(f - target) >= 0) {
+      if (n_freed) *n_freed = n;
+      break;
+    }
+    if ((spin & 63u) == 0u) {
+      std::lock_guard<std::mutex> lk(c->mu);
+      if (!running(c)) {
+        finalize_locked(c);
+        if (n_freed) *n_freed = n;
+        break;
+      }
+    }
+    const double us = std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count();
+    if (timeout_us > 0 && us > (double)timeout_us) {
+      if (n_freed) *n_freed = got;
+      return COOP_ETIMEOUT;
+    }
+    if (spin > 2048) std::this_thread::yield();
+  }
+  const double us = std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count();
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->gather_us_max = std::max(c->gather_us_max, us);
+  return COOP_OK;
+}
+
+coop_status coop_release(coop_ctx *c, int n) {
+  if (!c || n < 1) return COOP_EINVAL;
+  DeviceGuard guard(c->device);
+  std::lock_guard<std::mutex> lk(c->mu);
+  finalize_locked(c);
+  const uint32_t f = load_acquire(&c->mbox->freed);
+  if ((int32_t)(f - c->served) > 0) c->served = f;
+  const int held = (int)(c->served - c->returned);
+  if (n > held) return COOP_EINVAL;
+  c->returned += (uint32_t)n;
+  if (running(c)) {
+    switch (c->cur_mode) {
+      case MODE_BFS: launch_join<MODE_BFS>(c, n); break;
+      case MODE_SSSP: launch_join<MODE_SSSP>(c, n); break;
+      default: launch_join<MODE_BARRIER>(c, n); break;
+    }
+    cudaEventRecord(c->ev_join, c->join_stream);
+    if (cuda_failed(cudaGetLastError(), "fork launch")) return COOP_ECUDA;
+  }
+  return COOP_OK;
+}
+
+coop_status coop_sync(coop_ctx *c) {
+  if (!c) return COOP_EINVAL;
+  DeviceGuard guard(c->device);
+  if (c->launched && cudaEventSynchronize(c->ev_done) != cudaSuccess) return COOP_ECUDA;
+  if (cudaStreamSynchronize(c->join_stream) != cudaSuccess) return COOP_ECUDA;
+  std::lock_guard<std::mutex> lk(c->mu);
+  finalize_locked(c);
+  const int32_t e = __atomic_load_n(&c->mbox->err, __ATOMIC_ACQUIRE);
+  if (e != 0) return (coop_status)e;
+  return (coop_status)__atomic_load_n(&c->mbox->status, __ATOMIC_ACQUIRE);
+}
+
+coop_status coop_get_stats(coop_ctx *c, coop_stats *s) {
+  if (!c || !s) return COOP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (running(c)) return COOP_EBUSY;
+  finalize_locked(c);
+  const Mailbox *m = c->mbox;
+  memset(s, 0, sizeof(*s));
+  s->levels = m->levels;
+  s->barriers = m->barriers;
+  s->kills = m->kills;
+  s->forks = m->forks;
+  s->min_active = m->min_active;
+  s->max_active = m->max_active;
+  s->initial_active = m->initial_active;
+  s->edges_scanned = (int64_t)m->edges_scanned;
+  s->frontier_total = (int64_t)m->frontier_total;
+  s->gather_us_max = c->gather_us_max;
+  if (c->timing && c->launched) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev_t0, c->ev_t1) == cudaSuccess) s->kernel_us = 1000.0 * ms;
+    (void)cudaGetLastError();
+  }
+  int32_t status = m->err != 0 ? m->err : m->status;
+  if (c->launched && m->run_done != c->run && status == 0) status = COOP_ETIMEOUT;  // never finished cleanly
+  s->status = status;
+  return (coop_status)status;
+}
+
+coop_status coop_get_resize_log(coop_ctx *c, int32_t *out, int cap, int *n) {
+  if (!c || !n || cap < 0 || (cap > 0 && !out)) return COOP_EINVAL;
+  DeviceGuard guard(c->device);
+  *n = 0;
+  if (c->launched && cudaEventSynchronize(c->ev_done) != cudaSuccess) return COOP_ECUDA;
+  uint32_t ln = 0;
+  if (cudaMemcpy(&ln, &c->ctl->log_n, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return COOP_ECUDA;
+  const int take = std::min<int>((int)std::min<uint32_t>(ln, (uint32_t)kLogCap), cap);
+  if (take > 0 && cudaMemcpy(out, c->ctl->log, sizeof(LogRec) * (size_t)take, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return COOP_ECUDA;
+  *n = take;
+  return COOP_OK;
+}
+
+coop_status coop_set_schedule(coop_ctx *c, uint64_t seed, double p_kill, double p_fork, int reserve_ctas) {
+  if (!c || p_kill < 0.0 || p_kill > 1.0 || p_fork < 0.0 || p_fork > 1.0 || reserve_ctas < 0 ||
+      reserve_ctas > kMaxCtas)
+    return COOP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->sched_seed = seed;
+  c->p_kill = p_kill;
+  c->p_fork = p_fork;
+  c->reserve = reserve_ctas;
+  return COOP_OK;
+}
+
+coop_status coop_set_timeout(coop_ctx *c, int64_t timeout_us) {
+  if (!c || timeout_us < 1) return COOP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->timeout_us = timeout_us;
+  return COOP_OK;
+}
+
+coop_status coop_set_timing(coop_ctx *c, int on) {
+  if (!c) return COOP_EINVAL;
+  DeviceGuard guard(c->device);
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (on && !c->ev_t0) {
+    if (cudaEventCreate(&c->ev_t0) != cudaSuccess || cudaEventCreate(&c->ev_t1) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return COOP_ECUDA;
+    }
+  }
+  c->timing = on != 0;
+  return COOP_OK;
+}
+
+coop_status coop_query(coop_ctx *c, int *max_ctas, int *threads_per_cta, int *sm_count, int *lent) {
+  if (!c) return COOP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  finalize_locked(c);
+  if (max_ctas) *max_ctas = c->N;
+  if (threads_per_cta) *threads_per_cta = kWorkers;
+  if (sm_count) *sm_count = c->sm_count;
+  if (lent) *lent = (int)(c->served - c->returned);
+  return COOP_OK;
+}
+
+coop_status coop_saxpy(int n_ctas, int64_t n, float a, const float *d_x, float *d_y, coop_stream stream) {
+  if (n_ctas < 1 || n < 0 || (n > 0 && (!d_x || !d_y))) return COOP_EINVAL;
+  if (n == 0) return COOP_OK;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute((const void *)coop_saxpy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kCorunnerSmem);
+  });
+  coop_saxpy_kernel<<<n_ctas, 1024, kCorunnerSmem, (cudaStream_t)stream>>>(n, a, d_x, d_y);
+  return cuda_failed(cudaGetLastError(), "co-runner launch") ? COOP_ECUDA : COOP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,522 @@
+// coop_runtime.cuh - device runtime of the cooperative kernels (sm_103a).
+//
+// Implements the primitives of Sec. 3.1 of "Cooperative Kernels" (Sorensen, Evrard and
+// Donaldson, FSE 2017) for persistent CUDA kernels:
+//
+//  * active CTAs and logical ids: a CTA is *active* once admitted; active CTAs hold the
+//    contiguous logical ids [0, M-1]; logical id 0 (block 0 of the main launch, the
+//    master) is never killed.  Logical ids are decoupled from blockIdx so that CTAs of
+//    a later launch (forks) can take ids M..M+k-1.
+//  * resizing_global_barrier as the query barrier of Sec. 4.2: all active CTAs arrive
+//    on one L2-resident counter (acq_rel, gpu scope); the last arrival releases the
+//    barrier by bumping an epoch word (sense reversal by epoch parity).  Inside the
+//    release it (2) forks: admits up to N-M CTAs that are waiting to join, (3) queries
+//    the scheduler for W, (4) broadcasts the next interval (the transmitted state) and
+//    the new M; (5) the CTAs with logical ids >= M' leave.  Fork happens before kill,
+//    so ids [0, min(M, M')-1] are untouched (Sec. 3.1).
+//  * request_fork via join-on-arrival: every CTA other than the master first registers
+//    (takes a ticket) and waits for the release that admits it; a CTA counts towards M
+//    only after admission, so a launched-but-not-resident CTA never holds a barrier up.
+//  * transmit: the interval record (level, input queue, frontier size) is written by
+//    the releaser before the release and read by every CTA after it; joiners read the
+//    same record, which is "thread 0 of workgroup 0's" transmitted state since those
+//    values are uniform across the kernel (the observation of Appendix B).
+//  * the scheduler side of query(): a poller warp in the master CTA mirrors the host's
+//    request counter (mapped pinned memory, system scope) into device memory, so the
+//    barrier's release path reads only L2.
+//
+// Every spin-wait reads %globaltimer and gives up after the context's limit, setting a
+// sticky error that all other waits observe; nothing here can wait forever.
+#pragma once
+#include <stdint.h>
+
+namespace coopdev {
+
+constexpr int kWorkers = 992;               // worker threads per CTA (31 warps)
+constexpr int kWarps = kWorkers / 32;
+constexpr int kBlock = kWorkers + 32;       // + one scheduler (poller) warp = 1024
+constexpr int kMaxCtas = 2048;              // admission slot table; N <= kMaxCtas
+constexpr int kLogCap = 4096;               // resize-log records per run
+constexpr int kReserveSmem = 116 * 1024;    // dynamic smem of a traversal CTA
+constexpr int kCorunnerSmem = 116 * 1024;   // dynamic smem of a co-runner CTA (sum > SM capacity)
+constexpr uint64_t kEntryGatherNs = 20000;  // master waits this long for its launch to register
+
+enum Mode : int { MODE_BFS = 0, MODE_SSSP = 1, MODE_BARRIER = 2 };
+
+enum Err : int {
+  ERR_TIMEOUT = -4,   // COOP_ETIMEOUT
+  ERR_OVERFLOW = -6,  // COOP_EOVERFLOW
+  ERR_GRAPH = -7      // COOP_EGRAPH
+};
+
+// The transmitted state of one resizing-barrier interval (Fig. 4: level, in_nodes,
+// out_nodes) plus the active count M that holds during the interval.
+struct Interval {
+  int32_t M;       // active CTAs in this interval
+  int32_t level;   // BFS level / SSSP round whose frontier is expanded
+  uint32_t sel;    // input queue index; the output queue is sel ^ 1
+  uint32_t count;  // frontier vertices in the input queue
+  uint32_t edges;  // frontier out-edges (size of this interval's edge space)
+  uint32_t done;   // 1: the traversal is over, every CTA leaves
+  uint32_t epoch;  // epoch number that opened this interval
+  uint32_t pad;
+};
+
+struct LogRec {
+  int32_t m_before, k, w, m_after;
+};
+
+struct alignas(128) Word {
+  uint32_t v;
+  uint32_t pad[31];
+};
+
+// Control block in device memory (L2-resident), zeroed before every run.
+struct Ctl {
+  Word arrive;        // arrivals at the current barrier
+  Word epoch;         // release word: bumped by the releaser
+  Word join_ticket;   // registrations of CTAs waiting to be admitted
+  alignas(128) unsigned long long qctr[2];  // per queue: (vertices << 32) | edges
+  uint64_t pad_q[14];
+  alignas(128) Interval iv;  // the current interval (written only by releasers)
+  uint32_t pad_iv[24];
+  // header line: written once per run by the init kernel, then by error/done paths
+  alignas(128) uint32_t run;
+  uint32_t kill_req_mirror;  // written by the poller warp
+  uint32_t err;              // sticky error (negative coop_status as uint32)
+  uint32_t done;             // set by the final release
+  uint32_t ovf;              // SSSP distance overflow seen
+  uint32_t pad_h[27];
+  // releaser-private bookkeeping (serialised by the barrier)
+  alignas(128) uint32_t admitted;
+  uint32_t killed_host;
+  int32_t barriers, kills, forks, min_active, max_active, initial_active;
+  unsigned long long edges_scanned, frontier_total;
+  uint32_t log_n;
+  uint32_t pad_b[15];
+  alignas(128) unsigned long long slot[kMaxCtas];  // admission records, by ticket % kMaxCtas
+  LogRec log[kLogCap];
+};
+
+// Host <-> device mailbox in mapped pinned host memory.
+struct alignas(128) Mailbox {
+  uint32_t kill_req;  // host -> device: cumulative CTAs requested by the scheduler
+  uint32_t pad0[31];
+  uint32_t freed;     // device -> host: cumulative requested CTAs that have left
+  int32_t err;        // device -> host: sticky error of the current run
+  uint32_t run_done;  // device -> host: id of the last run that finished
+  uint32_t pad1[29];
+  int32_t levels, barriers, kills, forks, min_active, max_active, initial_active, status;
+  unsigned long long edges_scanned, frontier_total;
+};
+
+// Kernel parameters: immutable for the whole run and identical for forked CTAs
+// (Sec. 3.1, "the parameters to a cooperative kernel are immutable").
+struct Params {
+  const int32_t *row_off;
+  const int32_t *col;
+  const uint32_t *w;
+  int32_t *level;
+  uint32_t *dist;
+  uint32_t *visited;  // BFS: 1 bit per vertex
+  uint32_t *stamp;    // SSSP: frontier round each vertex was last queued for
+  uint32_t *qv[2];    // frontier queues: vertex id (SSSP)
+  uint32_t *qs[2];    //                  first column index (row_off[v])
+  uint32_t *qo[2];    //                  exclusive prefix of out-degrees (edge space)
+  Ctl *ctl;
+  Mailbox *mbox;
+  int32_t V;
+  uint32_t E;
+  int32_t src;
+  int32_t N;
+  uint32_t launched;   // CTAs in the main launch (the master waits for them at entry)
+  uint32_t kill_base;  // scheduler requests already served when the run started
+  uint64_t timeout_ns;
+  uint64_t sched_seed;
+  uint32_t p_kill;     // schedule: kill probability * 2^32 (0 = never)
+  uint32_t p_fork;     // schedule: fork probability * 2^32 (0 = never)
+  uint32_t sched_on;
+  uint32_t run;
+  int32_t n_barriers;  // MODE_BARRIER: intervals to run
+  uint32_t extra_wait; // barrier self-test: arrivals that never come
+  uint32_t coop;       // 0: non-cooperative baseline (fixed ids, no scheduler)
+};
+
+struct CtaShared {
+  Interval iv;
+  int32_t id;
+  int32_t ok;
+  int32_t exit;
+  int32_t workers_left;  // set when this CTA's worker warps have left (bounds the poller)
+};
+
+// ---------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint64_t gtime() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint64_t ld_acquire64(const unsigned long long *p) {
+  uint64_t v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed64(unsigned long long *p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t *p, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+// mapped pinned host memory: generic addressing, system scope
+__device__ __forceinline__ uint32_t ld_sys(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.sys.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_sys(uint32_t *p, uint32_t v) {
+  asm volatile("st.relaxed.sys.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_sys64(unsigned long long *p, uint64_t v) {
+  asm volatile("st.relaxed.sys.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void workers_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kWorkers) : "memory");
+}
+__device__ __forceinline__ unsigned lanemask_le() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_le;" : "=r"(m));
+  return m;
+}
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {  // SplitMix64 finaliser
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Read the interval record with strong (relaxed, gpu-scope) loads after an acquire.
+__device__ __forceinline__ Interval read_iv(const Ctl *c) {
+  Interval r;
+  const uint32_t *s = reinterpret_cast<const uint32_t *>(&c->iv);
+  uint32_t *d = reinterpret_cast<uint32_t *>(&r);
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(Interval) / 4); ++i) d[i] = ld_relaxed(s + i);
+  return r;
+}
+
+// ---------------------------------------------------------------- errors / stats
+__device__ __noinline__ void raise_err(const Params &p, int code) {
+  if (atomicCAS(&p.ctl->err, 0u, (uint32_t)code) == 0u) {
+    st_sys((uint32_t *)&p.mbox->err, (uint32_t)code);
+    __threadfence_system();
+  }
+}
+
+__device__ __noinline__ void publish_stats(const Params &p, int status) {
+  Ctl *c = p.ctl;
+  Mailbox *m = p.mbox;
+  st_sys((uint32_t *)&m->levels, (uint32_t)c->iv.level);
+  st_sys((uint32_t *)&m->barriers, (uint32_t)c->barriers);
+  st_sys((uint32_t *)&m->kills, (uint32_t)c->kills);
+  st_sys((uint32_t *)&m->forks, (uint32_t)c->forks);
+  st_sys((uint32_t *)&m->min_active, (uint32_t)c->min_active);
+  st_sys((uint32_t *)&m->max_active, (uint32_t)c->max_active);
+  st_sys((uint32_t *)&m->initial_active, (uint32_t)c->initial_active);
+  st_sys((uint32_t *)&m->status, (uint32_t)status);
+  st_sys64(&m->edges_scanned, c->edges_scanned);
+  st_sys64(&m->frontier_total, c->frontier_total);
+  __threadfence_system();
+  st_sys(&m->run_done, p.run);
+  __threadfence_system();
+}
+
+// ---------------------------------------------------------------- admission slots
+// slot = epoch << 32 | killed << 31 | logical id << 19 | (ticket & 0x7FFFF)
+__device__ __forceinline__ uint64_t slot_pack(uint32_t epoch, uint32_t killed, uint32_t id, uint32_t t) {
+  return ((uint64_t)epoch << 32) | ((uint64_t)(killed & 1u) << 31) | ((uint64_t)(id & 0xFFFu) << 19) |
+         (uint64_t)(t & 0x7FFFFu);
+}
+
+// Wait until the epoch word differs from `e` (a release happened).  false on error/timeout.
+__device__ __noinline__ bool wait_release(const Params &p, uint32_t e) {
+  Ctl *c = p.ctl;
+  const uint64_t t0 = gtime();
+  for (uint32_t spin = 0;; ++spin) {
+    if (ld_acquire(&c->epoch.v) != e) return true;
+    if (ld_relaxed(&c->err) != 0u) return false;
+    if ((spin & 31u) == 31u) {
+      if (gtime() - t0 > p.timeout_ns) {
+        raise_err(p, ERR_TIMEOUT);
+        return false;
+      }
+      __nanosleep(spin < 4096 ? 20 : 200);
+    }
+  }
+}
+
+// Wait until the epoch word reaches `e` (a joiner waiting for its admission release).
+__device__ __noinline__ bool wait_epoch_at_least(const Params &p, uint32_t e) {
+  Ctl *c = p.ctl;
+  const uint64_t t0 = gtime();
+  for (uint32_t spin = 0;; ++spin) {
+    if ((int32_t)(ld_acquire(&c->epoch.v) - e) >= 0) return true;
+    if (ld_relaxed(&c->err) != 0u) return false;
+    if ((spin & 31u) == 31u) {
+      if (gtime() - t0 > p.timeout_ns) {
+        raise_err(p, ERR_TIMEOUT);
+        return false;
+      }
+      __nanosleep(50);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- release (query barrier)
+// Runs in thread 0 of the last CTA to arrive, while every other active CTA waits.
+// Computes the next interval from the output queue, admits joiners (fork), asks the
+// scheduler for W (query), kills from the top, logs the resize and publishes.
+template <int MODE>
+__device__ __noinline__ Interval release_step(const Params &p, const Interval cur) {
+  Ctl *c = p.ctl;
+  Interval nxt = cur;
+  nxt.epoch = cur.epoch + 1u;
+  nxt.level = cur.level + 1;
+  uint32_t count, edges;
+  if (MODE == MODE_BARRIER) {
+    count = (cur.level + 1 < p.n_barriers) ? 1u : 0u;
+    edges = 0u;
+  } else {
+    const uint32_t out = cur.sel ^ 1u;
+    const unsigned long long packed = c->qctr[out];
+    count = (uint32_t)(packed >> 32);
+    edges = (uint32_t)packed;
+    c->qctr[cur.sel] = 0ull;  // the finished input queue becomes the next output queue
+    nxt.sel = out;
+  }
+  nxt.count = count;
+  nxt.edges = edges;
+  nxt.done = (count == 0u || ld_relaxed(&c->err) != 0u) ? 1u : 0u;
+
+  const int32_t M = cur.M;
+  int32_t k = 0, W = 0, Wh = 0;
+  uint32_t A = c->admitted;
+  if (!nxt.done && p.coop) {
+    // (2) fork: admit CTAs that registered and wait, up to N - M
+    const uint32_t R = ld_relaxed(&c->join_ticket.v);
+    k = (int32_t)min((uint32_t)(p.N - M), R - A);
+    int32_t Ws = 0;
+    if (p.sched_on) {
+      const uint64_t r = mix64(p.sched_seed ^ mix64((uint64_t)(c->barriers + 1)));
+      const uint64_t r2 = mix64(r);
+      const int32_t kcap = ((uint32_t)(r >> 32) < p.p_fork) ? (int32_t)(r2 % (uint64_t)(p.N - M + 1)) : 0;
+      k = min(k, kcap);
+      if ((uint32_t)r < p.p_kill) Ws = (int32_t)((r2 >> 32) % (uint64_t)M);
+    }
+    // (3) query: W = CTAs the scheduler still needs (never CTA 0)
+    const uint32_t req = ld_relaxed(&c->kill_req_mirror);
+    const int32_t pend = (int32_t)(req - p.kill_base - c->killed_host);
+    const int32_t ph = pend > 0 ? pend : 0;
+    W = min(ph + Ws, M + k - 1);
+    Wh = min(ph, W);
+  }
+  const int32_t Mn = M + k - W;
+  for (int32_t i = 0; i < k; ++i) {
+    const uint32_t t = A + (uint32_t)i;
+    const uint32_t idv = (uint32_t)(M + i);
+    st_relaxed64(&c->slot[t % kMaxCtas], slot_pack(nxt.epoch, idv >= (uint32_t)Mn, idv, t));
+  }
+  c->admitted = A + (uint32_t)k;
+  if (Wh > 0) {
+    c->killed_host += (uint32_t)Wh;
+    st_sys(&p.mbox->freed, p.kill_base + c->killed_host);
+  }
+  c->barriers += 1;
+  c->kills += W;
+  c->forks += k;
+  c->min_active = min(c->min_active, Mn);
+  c->max_active = max(c->max_active, Mn);
+  if (!nxt.done) {
+    c->edges_scanned += edges;
+    c->frontier_total += count;
+  }
+  if ((k | W) != 0 && c->log_n < (uint32_t)kLogCap) {
+    c->log[c->log_n] = LogRec{M, k, W, Mn};
+    c->log_n += 1u;
+  }
+  nxt.M = Mn;
+  c->iv = nxt;
+  if (nxt.done) {
+    st_relaxed(&c->done, 1u);
+    const uint32_t e = ld_relaxed(&c->err);
+    publish_stats(p, e ? (int)e : (ld_relaxed(&c->ovf) ? (int)ERR_OVERFLOW : 0));
+  }
+  return nxt;
+}
+
+// The resizing global barrier, called by all worker threads of an active CTA.
+// Returns false when the run is aborting (error or timeout).
+template <int MODE>
+__device__ __forceinline__ bool resizing_barrier(const Params &p, CtaShared &cs) {
+  workers_sync();  // the CTA's work for the interval is done
+  if (threadIdx.x == 0) {
+    Ctl *c = p.ctl;
+    const Interval cur = cs.iv;
+    const uint32_t old = atom_add_acq_rel(&c->arrive.v, 1u);
+    bool ok = true;
+    if (old == (uint32_t)(cur.M - 1) + p.extra_wait) {
+      const Interval nxt = release_step<MODE>(p, cur);
+      st_relaxed(&c->arrive.v, 0u);
+      st_release(&c->epoch.v, cur.epoch + 1u);
+      cs.iv = nxt;
+    } else {
+      ok = wait_release(p, cur.epoch);
+      if (ok) cs.iv = read_iv(c);
+    }
+    cs.ok = ok ? 1 : 0;
+  }
+  workers_sync();
+  return cs.ok != 0;
+}
+
+// ---------------------------------------------------------------- entry
+// A CTA that is not the master registers and waits for a release that admits it
+// (request_fork seen from the forked side).  Returns false if it should leave.
+__device__ __noinline__ bool join_enter(const Params &p, CtaShared &cs) {
+  Ctl *c = p.ctl;
+  if (ld_relaxed(&c->run) != p.run || ld_relaxed(&c->done) != 0u || ld_relaxed(&c->err) != 0u) return false;
+  const uint32_t t = atomicAdd(&c->join_ticket.v, 1u);
+  const uint64_t t0 = gtime();
+  uint64_t s = 0;
+  for (uint32_t spin = 0;; ++spin) {
+    s = ld_acquire64(&c->slot[t % kMaxCtas]);
+    if (s != 0ull && (uint32_t)(s & 0x7FFFFull) == (t & 0x7FFFFu)) break;
+    if (ld_relaxed(&c->done) != 0u || ld_relaxed(&c->err) != 0u || ld_relaxed(&c->run) != p.run) return false;
+    // a CTA that is never admitted simply leaves after the limit; it holds nobody up
+    if ((spin & 15u) == 15u && gtime() - t0 > 4ull * p.timeout_ns) return false;
+    __nanosleep(100);
+  }
+  if ((s >> 31) & 1ull) return false;  // admitted and killed in the same barrier
+  const uint32_t ea = (uint32_t)(s >> 32);
+  if (!wait_epoch_at_least(p, ea)) return false;
+  cs.iv = read_iv(c);
+  cs.id = (int32_t)((s >> 19) & 0xFFFull);
+  return true;
+}
+
+// Non-cooperative baseline entry: fixed id = blockIdx.x, wait for the master's start.
+__device__ __noinline__ bool plain_enter(const Params &p, CtaShared &cs) {
+  Ctl *c = p.ctl;
+  if (!wait_epoch_at_least(p, 1u)) return false;
+  cs.iv = read_iv(c);
+  cs.id = (int32_t)blockIdx.x;
+  return true;
+}
+
+// The master (block 0 of the main launch, logical id 0) seeds the frontier, waits
+// briefly for its launch to register, admits them and opens interval 1 (level 0).
+template <int MODE>
+__device__ __noinline__ void master_enter(const Params &p, CtaShared &cs) {
+  Ctl *c = p.ctl;
+  uint32_t count = 0u, edges = 0u;
+  if (MODE == MODE_BARRIER) {
+    count = p.n_barriers > 0 ? 1u : 0u;
+  } else {
+    const int32_t s = p.src;
+    const int32_t rs = __ldg(p.row_off + s), re = __ldg(p.row_off + s + 1);
+    if (rs < 0 || re < rs || (uint32_t)re > p.E) {
+      raise_err(p, ERR_GRAPH);
+    } else {
+      if (MODE == MODE_BFS) {
+        p.level[s] = 0;
+        atomicOr(p.visited + (s >> 5), 1u << (s & 31));
+      } else {
+        p.dist[s] = 0u;
+        p.stamp[s] = 1u;
+      }
+      if (re > rs) {
+        p.qo[0][0] = 0u;
+        p.qs[0][0] = (uint32_t)rs;
+        p.qv[0][0] = (uint32_t)s;
+        count = 1u;
+        edges = (uint32_t)(re - rs);
+      }
+    }
+  }
+  int32_t k = 0;
+  if (p.coop) {
+    const uint64_t t0 = gtime();
+    while (ld_relaxed(&c->join_ticket.v) + 1u < p.launched && gtime() - t0 < kEntryGatherNs) __nanosleep(200);
+    const uint32_t R = ld_relaxed(&c->join_ticket.v);
+    k = (int32_t)min(R, (uint32_t)(p.N - 1));
+    for (int32_t i = 0; i < k; ++i)
+      st_relaxed64(&c->slot[(uint32_t)i % kMaxCtas], slot_pack(1u, 0u, (uint32_t)(1 + i), (uint32_t)i));
+  } else {
+    k = (int32_t)gridDim.x - 1;
+  }
+  Interval iv;
+  iv.M = 1 + k;
+  iv.level = 0;
+  iv.sel = 0u;
+  iv.count = count;
+  iv.edges = edges;
+  iv.done = (count == 0u || ld_relaxed(&c->err) != 0u) ? 1u : 0u;
+  iv.epoch = 1u;
+  iv.pad = 0u;
+  c->admitted = (uint32_t)k;
+  c->initial_active = iv.M;
+  c->min_active = iv.M;
+  c->max_active = iv.M;
+  c->edges_scanned = edges;
+  c->frontier_total = count;
+  c->iv = iv;
+  if (iv.done) {
+    st_relaxed(&c->done, 1u);
+    const uint32_t e = ld_relaxed(&c->err);
+    publish_stats(p, (int)e);
+  }
+  st_release(&c->epoch.v, 1u);
+  cs.iv = iv;
+  cs.id = 0;
+}
+
+// The scheduler side of query(): mirror the host's request counter into L2.  Runs in
+// the master CTA until the run is over or the master's own workers have left.
+__device__ __noinline__ void poller(const Params &p, const volatile int32_t *workers_left) {
+  Ctl *c = p.ctl;
+  uint32_t last = p.kill_base;
+  for (;;) {
+    const uint32_t r = ld_sys(&p.mbox->kill_req);
+    if (r != last) {
+      st_relaxed(&c->kill_req_mirror, r);
+      last = r;
+    }
+    if (ld_relaxed(&c->done) != 0u || ld_relaxed(&c->err) != 0u || *workers_left != 0) return;
+    __nanosleep(500);
+  }
+}
+
+}  // namespace coopdev

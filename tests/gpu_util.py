@@ -1,0 +1,43 @@
+"""Helpers shared by the GPU tests: move seeded host graphs to the device, run, compare."""
+import numpy as np
+
+import paper_1707_01989_gb300 as coop
+
+
+class DevGraph:
+    """A host CSR (graphgen.CSR) mirrored on the device; keeps the tensors alive."""
+
+    def __init__(self, g, w=None, device="cuda:0"):
+        import torch
+        self.g = g
+        self.ro = torch.from_numpy(np.array(g.row_off)).to(device)
+        self.col = torch.from_numpy(np.array(g.col)).to(device)
+        self.w = None if w is None else torch.from_numpy(np.ascontiguousarray(w).view(np.int32)).to(device)
+        self.csr = coop.make_csr(self.ro, self.col)
+        self.device = device
+
+    def empty(self):
+        import torch
+        return torch.empty(self.g.num_vertices, dtype=torch.int32, device=self.device)
+
+
+def run_bfs(ctx, dg, src, baseline=False, ok=(coop.COOP_OK,)):
+    out = dg.empty()
+    f = coop.coop_bfs_baseline if baseline else coop.coop_bfs
+    st = f(ctx, dg.csr, src, out, stats=True, ok=ok)
+    return out.cpu().numpy(), st
+
+
+def run_sssp(ctx, dg, src, baseline=False, ok=(coop.COOP_OK,)):
+    out = dg.empty()
+    f = coop.coop_sssp_baseline if baseline else coop.coop_sssp
+    st = f(ctx, dg.csr, dg.w, src, out, stats=True, ok=ok)
+    return out.cpu().numpy().view(np.uint32), st
+
+
+def assert_same(got, exp, what):
+    got = np.asarray(got)
+    exp = np.asarray(exp)
+    assert got.shape == exp.shape, (what, got.shape, exp.shape)
+    bad = np.flatnonzero(got != exp)
+    assert bad.size == 0, f"{what}: {bad.size} mismatches, first at {bad[0]}: got {got[bad[0]]} expected {exp[bad[0]]}"

@@ -1,0 +1,201 @@
+"""Cooperative behaviour on the GPU: forced kill/fork schedules, the host arbiter, timeouts.
+
+Schedule invariance (Sec. 3.1: an offer_kill may always be a no-op and k = 0 forks is
+always legal, so every schedule must give the same result): random seeded schedules
+must leave BFS levels and SSSP distances bit-identical to the oracle, and every resize
+the device logs must be a legal Fork/Kill sequence of the operational semantics
+(Appendix A), replayed on oracle.semantics.
+"""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+import paper_1707_01989_gb300 as coop
+from gpu_util import DevGraph, assert_same, run_bfs, run_sssp
+from oracle.semantics import replay_resize_log
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture()
+def ctx(cuda_device):
+    c = coop.coop_init(0)
+    yield c
+    coop.coop_destroy(c)
+
+
+def _replay(ctx, st):
+    log = coop.coop_get_resize_log(ctx)
+    N = coop.coop_query(ctx)["max_ctas"]
+    model = replay_resize_log(N, st.initial_active, log)
+    assert sum(r[1] for r in log) == st.forks
+    assert sum(r[2] for r in log) == st.kills
+    assert min([st.initial_active] + [r[3] for r in log]) == st.min_active
+    return log, model
+
+
+@pytest.mark.parametrize("seed", range(32))
+def test_random_schedules_bfs_bit_exact(ctx, seed):
+    g = gg.rmat(13, 16, seed=seed % 4) if seed % 3 else gg.grid(64, 64)
+    src = gg.max_out_degree_vertex(g) if seed % 3 else 0
+    N = coop.coop_query(ctx)["max_ctas"]
+    coop.coop_set_schedule(ctx, seed, p_kill=0.3, p_fork=0.5, reserve_ctas=N)
+    lv, st = run_bfs(ctx, DevGraph(g), src)
+    assert_same(lv, oracle.bfs(g, src), f"schedule {seed}")
+    log, _ = _replay(ctx, st)
+    if st.barriers > 8:
+        assert st.kills > 0  # the schedule really resized the kernel
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_schedules_sssp_bit_exact(ctx, seed):
+    g = gg.rmat(13, 16, seed=10 + seed % 3)
+    w = gg.weights(g, seed)
+    src = gg.max_out_degree_vertex(g)
+    N = coop.coop_query(ctx)["max_ctas"]
+    coop.coop_set_schedule(ctx, 1000 + seed, p_kill=0.4, p_fork=0.4, reserve_ctas=N // 2)
+    d, st = run_sssp(ctx, DevGraph(g, w), src)
+    assert_same(d, oracle.dijkstra(g, w, src), f"sssp schedule {seed}")
+    _replay(ctx, st)
+
+
+def test_kill_at_every_barrier(ctx):
+    """A schedule that accepts kills at every barrier only ever shrinks M, never below 1."""
+    g = gg.rmat(12, 8, seed=2)
+    src = gg.max_out_degree_vertex(g)
+    coop.coop_set_schedule(ctx, 5, p_kill=1.0, p_fork=0.0, reserve_ctas=0)
+    lv, st = run_bfs(ctx, DevGraph(g), src)
+    assert_same(lv, oracle.bfs(g, src), "kill at every barrier")
+    log, _ = _replay(ctx, st)
+    assert all(r[1] == 0 for r in log)
+    assert [r[3] for r in log] == sorted([r[3] for r in log], reverse=True)
+    assert st.min_active >= 1 and st.forks == 0
+
+
+def test_master_alone(ctx):
+    """With N-1 CTAs lent to the host, the traversal runs on CTA 0 alone (M = 1 is legal)."""
+    N = coop.coop_query(ctx)["max_ctas"]
+    assert coop.coop_request_resources(ctx, N - 1) == N - 1
+    g = gg.rmat(12, 8, seed=2)
+    w = gg.weights(g, 3)
+    src = gg.max_out_degree_vertex(g)
+    dg = DevGraph(g, w)
+    lv, st = run_bfs(ctx, dg, src)
+    assert_same(lv, oracle.bfs(g, src), "master alone bfs")
+    assert st.max_active == 1 and st.min_active == 1
+    d, _ = run_sssp(ctx, dg, src)
+    assert_same(d, oracle.dijkstra(g, w, src), "master alone sssp")
+    coop.coop_release(ctx, N - 1)
+    lv, st = run_bfs(ctx, dg, src)
+    assert st.initial_active > 1
+
+
+def test_host_request_and_release_during_run(ctx):
+    """The scheduler takes half the CTAs from a running kernel, runs the co-runner on
+    the freed SMs, and gives them back (Sec. 4.2)."""
+    import torch
+    N = coop.coop_query(ctx)["max_ctas"]
+    half = N // 2
+    s = torch.cuda.Stream()
+    coop.coop_barrier_bench(ctx, 400000, stream=s, stats=False)
+    time.sleep(0.02)
+    t0 = time.perf_counter()
+    got = coop.coop_request_resources(ctx, half, timeout_us=2_000_000)
+    gather_ms = (time.perf_counter() - t0) * 1e3
+    assert got == half
+    assert coop.coop_query(ctx)["lent"] == half
+    x = torch.arange(1 << 22, dtype=torch.float32, device="cuda")
+    y = torch.ones_like(x)
+    cs = torch.cuda.Stream(priority=-1)
+    coop.coop_saxpy(half, 2.0, x, y, stream=cs)
+    cs.synchronize()
+    torch.testing.assert_close(y, 2.0 * x + 1.0)
+    coop.coop_release(ctx, half)
+    assert coop.coop_query(ctx)["lent"] == 0
+    assert coop.coop_sync(ctx) == coop.COOP_OK
+    st = coop.coop_get_stats(ctx)
+    log, model = _replay(ctx, st)
+    assert st.kills >= half and st.forks >= 1
+    assert any(r[2] == half for r in log)
+    assert gather_ms < 1000
+
+
+def test_request_with_no_run_in_flight_is_granted(ctx):
+    N = coop.coop_query(ctx)["max_ctas"]
+    assert coop.coop_request_resources(ctx, 3) == 3
+    g = gg.rmat(11, 8, seed=1)
+    src = gg.max_out_degree_vertex(g)
+    lv, st = run_bfs(ctx, DevGraph(g), src)
+    assert st.max_active <= N - 3  # the traversal ran without the lent CTAs
+    assert_same(lv, oracle.bfs(g, src), "with lent ctas")
+    coop.coop_release(ctx, 3)
+    with pytest.raises(coop.CoopError):
+        coop.coop_request_resources(ctx, N)  # CTA 0 is never surrendered
+
+
+def test_concurrent_requests_from_another_thread(ctx):
+    """Random request/release traffic from a host thread while traversals run."""
+    import torch
+    g = gg.rmat(16, 16, seed=3)
+    w = gg.weights(g, 4)
+    src = gg.max_out_degree_vertex(g)
+    dg = DevGraph(g, w)
+    exp_l, exp_d = oracle.bfs(g, src), oracle.dijkstra(g, w, src)
+    stop = threading.Event()
+    errors = []
+
+    def arbiter():
+        rng = np.random.default_rng(0)
+        try:
+            while not stop.is_set():
+                n = int(rng.integers(1, 40))
+                got = coop.coop_request_resources(ctx, n, timeout_us=500_000)
+                time.sleep(0.0005)
+                coop.coop_release(ctx, got)
+        except Exception as exc:  # surfaced below
+            errors.append(exc)
+
+    t = threading.Thread(target=arbiter)
+    t.start()
+    try:
+        for i in range(10):
+            lv, _ = run_bfs(ctx, dg, src)
+            assert_same(lv, exp_l, f"bfs under arbiter {i}")
+            d, _ = run_sssp(ctx, dg, src)
+            assert_same(d, exp_d, f"sssp under arbiter {i}")
+    finally:
+        stop.set()
+        t.join()
+    assert not errors, errors
+    coop.coop_sync(ctx)
+
+
+def test_barrier_wait_times_out_cleanly(ctx):
+    """A barrier waiting for arrivals that never come returns COOP_ETIMEOUT (no hang, no
+    fault) and the context keeps working."""
+    coop.coop_set_timeout(ctx, 200_000)
+    t0 = time.perf_counter()
+    st = coop.coop_barrier_bench(ctx, 10, never_arrive=1, ok=(coop.COOP_ETIMEOUT,))
+    assert st.status == coop.COOP_ETIMEOUT
+    assert time.perf_counter() - t0 < 10
+    coop.coop_set_timeout(ctx, 2_000_000)
+    st = coop.coop_barrier_bench(ctx, 1000)
+    assert st.status == coop.COOP_OK and st.barriers == 1000
+    g = gg.grid(30, 30)
+    lv, _ = run_bfs(ctx, DevGraph(g), 0)
+    assert_same(lv, oracle.bfs(g, 0), "after timeout")
+
+
+def test_saxpy_ragged(ctx):
+    import torch
+    for n in (1, 3, 1000, (1 << 20) + 3):
+        x = torch.randn(n, device="cuda")
+        y = torch.randn(n, device="cuda")
+        ref = 3.0 * x + y
+        coop.coop_saxpy(7, 3.0, x, y)
+        torch.cuda.synchronize()
+        torch.testing.assert_close(y, ref)
