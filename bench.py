@@ -37,12 +37,17 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "BFS/SSSP GTEPS (1 GB300, % HBM roofline); barrier us; co-runner p99 latency"
-WORKLOAD = "rmat20-sssp"
+WORKLOADS = {
+    # name: (graph kind, scale, graph seed, weight seed, traversal)
+    "rmat20-sssp": ("rmat", 20, 20, 21, "sssp"),   # the headline configuration
+    "rmat22-bfs": ("rmat", 22, 22, None, "bfs"),
+    "grid256-bfs": ("grid", 256, None, None, "bfs"),
+}
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of coop_traverse<SSSP> on the
-# workload above, from the ncu capture summarised in profiles/; valid only for the
-# kernel sources with this digest (otherwise reported as null).
-TRAFFIC = {"sources_sha": None, "bytes": None}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the persistent kernel, per
+# workload, from the ncu captures summarised in profiles/; an entry is used only while
+# the kernel sources still have the digest it was taken on (otherwise null).
+TRAFFIC = {}
 
 
 def sources_sha() -> str:
@@ -117,11 +122,15 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def load_workload(scale=20, seed=20, wseed=21):
+def load_workload(name="rmat20-sssp"):
+    """(graph, weights or None, source, traversal) of a named workload."""
     import graphgen as gg
+    kind, scale, seed, wseed, trav = WORKLOADS[name]
+    if kind == "grid":
+        return gg.grid(scale, scale), None, 0, trav
     g = gg.rmat(scale, 16, seed=seed)
-    w = gg.weights(g, wseed)
-    return g, w, gg.max_out_degree_vertex(g)
+    w = gg.weights(g, wseed) if wseed is not None else None
+    return g, w, gg.max_out_degree_vertex(g), trav
 
 
 def reached_work(g, reached_mask):
@@ -130,43 +139,72 @@ def reached_work(g, reached_mask):
     return int(reached_mask.sum()), int(deg[reached_mask].sum())
 
 
-def time_cpu_oracle(g, w, src, budget_s=10.0, max_runs=8):
-    """Time the oracle's Dijkstra as it stands (one core), whole traversals until budget."""
+def oracle_run(g, w, src, trav):
     import oracle
-    times = []
+    return oracle.dijkstra(g, w, src) if trav == "sssp" else oracle.bfs(g, src)
+
+
+def reached_of(out, trav):
+    import numpy as np
+    return (out != np.uint32(0xFFFFFFFF)) if trav == "sssp" else (out >= 0)
+
+
+def algorithmic_bytes(V, vr, es, trav):
+    """Bytes a work-efficient traversal must touch (per launch): init of the output array,
+    per reached vertex its queue write+read, row offsets and result update, per scanned
+    edge its column (+ weight) and the target's state."""
+    return 4 * V + 24 * vr + 12 * es if trav == "sssp" else 4 * V + 20 * vr + 8 * es
+
+
+def time_cpu_oracle(g, w, src, trav, budget_s=10.0, max_runs=8):
+    """Time the oracle as it stands (one core), whole traversals until the budget is spent."""
+    times, out = [], None
     t_start = time.perf_counter()
-    while len(times) < max_runs and (time.perf_counter() - t_start) < budget_s:
+    while len(times) < max_runs and (len(times) == 0 or (time.perf_counter() - t_start) < budget_s):
         t0 = time.perf_counter()
-        d = oracle.dijkstra(g, w, src)
+        out = oracle_run(g, w, src, trav)
         times.append(time.perf_counter() - t0)
-    return d, times
+    return out, times
+
+
+def config_of(name, g, extra=None):
+    kind, scale, seed, wseed, trav = WORKLOADS[name]
+    c = {"workload": name, "graph": kind, "V": g.num_vertices, "E": g.num_edges, "traversal": trav}
+    if kind == "rmat":
+        c.update({"scale": scale, "edge_factor": 16, "abcd": [0.57, 0.19, 0.19, 0.05], "seed": seed})
+        if wseed is not None:
+            c.update({"weights": "uint32 U[1,255]", "weight_seed": wseed})
+    else:
+        c.update({"grid": f"{scale}x{scale}", "neighbourhood": 4})
+    if extra:
+        c.update(extra)
+    return c
 
 
 def run_reference(args):
     """--impl reference: the CPU oracle on the same workload (rank 0 only)."""
-    import numpy as np
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    g, w, src = load_workload()
-    import oracle
+    g, w, src, trav = load_workload(args.workload)
     for _ in range(args.warmup):
-        oracle.dijkstra(g, w, src)
+        oracle_run(g, w, src, trav)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        d = oracle.dijkstra(g, w, src)
+        out = oracle_run(g, w, src, trav)
         times.append(time.perf_counter() - t0)
-    _, es = reached_work(g, d != np.uint32(0xFFFFFFFF))
+    _, es = reached_work(g, reached_of(out, trav))
     t = statistics.mean(times)
     val = es / t / 1e9
+    algo = "binary-heap Dijkstra" if trav == "sssp" else "FIFO-queue BFS"
     line = {
         "impl": "reference", "metric": METRIC, "value": round(val, 6), "unit": "GTEPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "scale": 20, "edge_factor": 16, "V": g.num_vertices, "E": g.num_edges},
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32" if trav == "sssp" else "int32", "data": "synthetic",
+        "config": config_of(args.workload, g, {"source": src}),
         "cpu_baseline": {"value": round(val, 6), "unit": "GTEPS", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} full Dijkstra traversals of the rmat20 workload"},
+                         "sample": f"{args.steps} full {algo} traversals of the {args.workload} workload"},
         "e2e": {"value": round(val, 6), "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -179,8 +217,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat20-sssp", choices=sorted(WORKLOADS))
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--threads", type=int, default=0, help="worker threads per CTA (0 = library default)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -200,31 +240,37 @@ def main():
     dev = torch.device("cuda", local)
     args.warmup = max(3, args.warmup)
 
-    g, w, src = load_workload()
+    g, w, src, trav = load_workload(args.workload)
     V, E = g.num_vertices, g.num_edges
     ro_h = torch.from_numpy(np.array(g.row_off)).pin_memory()
     col_h = torch.from_numpy(np.array(g.col)).pin_memory()
-    w_h = torch.from_numpy(w.view(np.int32)).pin_memory()
-    ro, col, wt = ro_h.to(dev), col_h.to(dev), w_h.to(dev)
-    dist_d = torch.empty(V, dtype=torch.int32, device=dev)
-    dist_h = torch.empty(V, dtype=torch.int32).pin_memory()
+    w_h = torch.from_numpy(w.view(np.int32)).pin_memory() if w is not None else None
+    ro, col = ro_h.to(dev), col_h.to(dev)
+    wt = w_h.to(dev) if w_h is not None else None
+    out_d = torch.empty(V, dtype=torch.int32, device=dev)
+    out_h = torch.empty(V, dtype=torch.int32).pin_memory()
     csr = coop.make_csr(ro, col)
-    ctx = coop.coop_init(local)
+    ctx = coop.coop_init(local, 0, args.threads)
     coop.coop_set_timing(ctx, True)
+    threads = coop.coop_query(ctx)["threads_per_cta"]
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
-    def step():
-        coop.coop_sssp(ctx, csr, wt, src, dist_d, stream=stream)
+    if trav == "sssp":
+        def step():
+            coop.coop_sssp(ctx, csr, wt, src, out_d, stream=stream)
+    else:
+        def step():
+            coop.coop_bfs(ctx, csr, src, out_d, stream=stream)
 
-    # correctness of what we time: one run against the oracle's invariants below
     for _ in range(args.warmup):
         step()
     stream.synchronize()
     st = coop.coop_get_stats(ctx)
-    d = dist_d.cpu().numpy().view(np.uint32)
-    reached = d != np.uint32(0xFFFFFFFF)
-    vr, es = reached_work(g, reached)
+    res = out_d.cpu().numpy()
+    if trav == "sssp":
+        res = res.view(np.uint32)
+    vr, es = reached_work(g, reached_of(res, trav))
 
     if world > 1:
         dist.barrier()
@@ -253,13 +299,16 @@ def main():
 
     # roofline of the dominant kernel (the persistent traversal kernel)
     hbm, peak_kind = peaks()
-    B = 4 * V + 24 * vr + 12 * es
+    B = algorithmic_bytes(V, vr, es, trav)
     k_s = statistics.mean(kern_us) / 1e6
     achieved = B / k_s / 1e9
-    traffic = TRAFFIC["bytes"] if TRAFFIC["sources_sha"] == sources_sha() else None
+    traffic = None
+    tr = TRAFFIC.get(args.workload)
+    if tr and tr.get("sources_sha") == sources_sha():
+        traffic = tr["bytes"]
 
     # end to end through the C ABI with host buffers: H2D inputs, traversal, D2H result
-    h2d = (V + 1) * 4 + E * 4 + E * 4
+    h2d = (V + 1) * 4 + E * 4 + (E * 4 if wt is not None else 0)
     d2h = V * 4
     e2e_ms = []
     for i in range(args.warmup + args.steps):
@@ -271,39 +320,38 @@ def main():
         with torch.cuda.stream(stream):
             ro.copy_(ro_h, non_blocking=True)
             col.copy_(col_h, non_blocking=True)
-            wt.copy_(w_h, non_blocking=True)
+            if wt is not None:
+                wt.copy_(w_h, non_blocking=True)
         step()
         with torch.cuda.stream(stream):
-            dist_h.copy_(dist_d, non_blocking=True)
+            out_h.copy_(out_d, non_blocking=True)
         e1.record(stream)
         e1.synchronize()
         if i >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
     e2e_val = es * world / (statistics.mean(e2e_ms) / 1e3) / 1e9
 
-    extras = {}
-    cpu = None
     if rank == 0:
+        extras = {}
         if not args.no_extras:
             extras = secondary(coop, ctx, dev, stream, flush, args)
-        dref, times = time_cpu_oracle(g, w, src, budget_s=args.cpu_budget)
-        parity = bool(np.array_equal(dref, d))
+        ref, times = time_cpu_oracle(g, w, src, trav, budget_s=args.cpu_budget)
+        extras["parity_vs_oracle"] = bool(np.array_equal(ref, res))
+        algo = "binary-heap Dijkstra" if trav == "sssp" else "FIFO-queue BFS"
         cpu = {"value": round(es / statistics.mean(times) / 1e9, 6), "unit": "GTEPS", "cores": 1, "kind": "oracle",
-               "sample": f"{len(times)} full Dijkstra traversal(s) of the rmat20 workload on 1 host core "
+               "sample": f"{len(times)} full {algo} traversal(s) of the {args.workload} workload on 1 host core "
                          f"({os.cpu_count()} cores present)"}
-        extras["parity_vs_oracle"] = parity
-
         line = {
             "metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(t_step * 1e3, 4), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "scale": 20, "edge_factor": 16, "V": V, "E": E, "V_reached": vr,
-                       "E_s": es, "source": src, "weights": "uint32 U[1,255]", "parallelism": "replicas",
-                       "l2": "flushed between steps (512 MB write)", "ctas": st.max_active,
-                       "threads_per_cta": 992},
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32" if trav == "sssp" else "int32",
+            "data": "synthetic",
+            "config": config_of(args.workload, g, {
+                "V_reached": vr, "E_s": es, "source": src, "parallelism": "replicas",
+                "l2": "flushed between steps (512 MB write)", "ctas": st.max_active, "threads_per_cta": threads}),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                          "frac": round(achieved / hbm, 4), "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "coop_traverse<SSSP>", "kernel_us": round(k_s * 1e6, 2),
+                         "kernel": f"coop_traverse<{trav.upper()}>", "kernel_us": round(k_s * 1e6, 2),
                          "algorithmic_bytes": B},
             "e2e": {"value": round(e2e_val, 4), "unit": "GTEPS", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -311,7 +359,7 @@ def main():
             "clocks": clocks.summary(),
             "cpu_baseline": cpu,
             "stats": {"levels": st.levels, "barriers": st.barriers, "frontier_total": st.frontier_total,
-                      "relaxation_edges": st.edges_scanned, "work_inflation": round(st.edges_scanned / es, 3)},
+                      "edges_expanded": st.edges_scanned, "work_inflation": round(st.edges_scanned / max(es, 1), 3)},
             "extras": extras,
         }
         print(json.dumps(line), flush=True)

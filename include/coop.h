@@ -15,7 +15,8 @@
  *  - Every pointer argument named d_* or inside coop_csr is DEVICE memory owned by the
  *    caller (e.g. a torch tensor); it must stay valid until the traversal's stream
  *    has synchronised.  Scratch (frontier queues, visited bitmap, control block) and
- *    the host mailbox are owned by the context.
+ *    the host mailbox are owned by the context.  A traversal's stream completes only
+ *    after every CTA it forked has left.
  *  - Calls return coop_status; negative values are errors.  No call aborts or throws.
  *  - A coop_stream is a cudaStream_t (same type, declared here without CUDA headers);
  *    NULL is the legacy default stream.
@@ -25,6 +26,11 @@
  *    touching memory out of range.
  *  - One context drives one traversal at a time.  coop_request_resources and
  *    coop_release may be called from another host thread while a traversal runs.
+ *    Device-synchronising CUDA calls (cudaMalloc, cudaFree, work on the legacy default
+ *    stream) made while a traversal runs wait for it to finish, and so does the first
+ *    launch of a kernel whose module is loaded lazily; a co-running task must allocate
+ *    its buffers and launch its kernels once beforehand, and use its own non-blocking
+ *    stream.  coop_init loads all of this library's kernels eagerly.
  */
 #ifndef COOP_H
 #define COOP_H
@@ -67,6 +73,8 @@ typedef struct {
     int32_t max_active;     /* largest active CTA count M seen */
     int32_t initial_active; /* M after the entry barrier */
     int32_t status;         /* coop_status of the run */
+    int32_t ctas_launched;  /* CTAs launched for the run: main grid + every forked CTA */
+    int32_t reserved;
     int64_t edges_scanned;  /* sum of out-degrees over every frontier (BFS: E_s) */
     int64_t frontier_total; /* sum of frontier sizes */
     double gather_us_max;   /* longest coop_request_resources wait during the run */
@@ -76,7 +84,8 @@ typedef struct {
 /*
  * Create a context on `device`.  max_ctas is N, the launch limit of Sec. 3.1
  * ("a maximum of N workgroups"); 0 picks every CTA that can be co-resident (one per
- * SM).  threads_per_cta must be 0 (default) or the compiled worker count (992).
+ * SM).  threads_per_cta is the number of worker threads per CTA: 0 (default, 992),
+ * 992, 736 or 480 (31, 23 or 15 worker warps; each CTA adds one scheduler warp).
  * Allocates the control block and a mapped pinned mailbox.  *out = NULL on error.
  */
 coop_status coop_init(int device, int max_ctas, int threads_per_cta, coop_ctx **out);
@@ -116,10 +125,11 @@ coop_status coop_request_resources(coop_ctx *ctx, int n_ctas, int timeout_us, in
 
 /*
  * Return n_ctas lent CTAs (Sec. 4.2: the scheduler signals that extra workgroups
- * should join at the next request_fork).  If a traversal is running, n_ctas new CTAs
- * are launched on the context's join stream; they join at the next resizing barrier
- * with the transmitted state of the running interval.  Otherwise the next traversal
- * simply starts with them.  COOP_EINVAL if more than are lent.
+ * should join at the next request_fork).  If a traversal is running, the running
+ * kernel launches n_ctas new CTAs of itself from the device (a follow-up launch into a
+ * fire-and-forget stream); they join at a resizing barrier with the transmitted state
+ * of the running interval.  Otherwise the next traversal simply starts with them.
+ * COOP_EINVAL if more than are lent.  Never blocks.
  */
 coop_status coop_release(coop_ctx *ctx, int n_ctas);
 
@@ -138,15 +148,12 @@ coop_status coop_get_resize_log(coop_ctx *ctx, int32_t *out, int cap, int *n);
 
 /*
  * Forced random schedule (tests and the multitasking benchmark).  At every resizing
- * barrier, with probability p_kill the scheduler accepts W in [0, M-1] offer_kills,
- * and with probability p_fork it grants up to k in [0, N-M] forks (taken from CTAs
- * waiting to join).  reserve_ctas extra CTAs are launched with each traversal on the
- * join stream; they occupy SMs that killed CTAs free and wait there to be forked.
- * p_kill = p_fork = 0 disables the schedule (the default).  Draws are SplitMix64
- * hashes of (seed, barrier index).
+ * barrier, with probability p_kill the scheduler accepts W in [0, M-1] offer_kills, and
+ * with probability p_fork it grants k in [0, N-M] new CTAs, which the kernel launches
+ * from the device at once and admits when they arrive.  p_kill = p_fork = 0 disables
+ * the schedule (the default).  Draws are SplitMix64 hashes of (seed, barrier index).
  */
-coop_status coop_set_schedule(coop_ctx *ctx, uint64_t seed, double p_kill, double p_fork,
-                              int reserve_ctas);
+coop_status coop_set_schedule(coop_ctx *ctx, uint64_t seed, double p_kill, double p_fork);
 
 /* Time limit for every device-side wait (default 2 s).  Exceeding it ends the run with COOP_ETIMEOUT. */
 coop_status coop_set_timeout(coop_ctx *ctx, int64_t timeout_us);

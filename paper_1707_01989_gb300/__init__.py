@@ -52,6 +52,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int32), ("barriers", ctypes.c_int32), ("kills", ctypes.c_int32),
                 ("forks", ctypes.c_int32), ("min_active", ctypes.c_int32), ("max_active", ctypes.c_int32),
                 ("initial_active", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("ctas_launched", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("edges_scanned", ctypes.c_int64), ("frontier_total", ctypes.c_int64),
                 ("gather_us_max", ctypes.c_double), ("kernel_us", ctypes.c_double)]
 
@@ -93,7 +94,7 @@ def load_library():
                 "coop_sync": [vp],
                 "coop_get_stats": [vp, sp],
                 "coop_get_resize_log": [vp, ctypes.POINTER(i32), ctypes.c_int, ip],
-                "coop_set_schedule": [vp, u64, ctypes.c_double, ctypes.c_double, ctypes.c_int],
+                "coop_set_schedule": [vp, u64, ctypes.c_double, ctypes.c_double],
                 "coop_set_timeout": [vp, i64],
                 "coop_set_timing": [vp, ctypes.c_int],
                 "coop_query": [vp, ip, ip, ip, ip],
@@ -282,9 +283,9 @@ def coop_get_resize_log(ctx, cap: int = 4096):
     return [tuple(buf[4 * i: 4 * i + 4]) for i in range(n.value)]
 
 
-def coop_set_schedule(ctx, seed: int, p_kill: float, p_fork: float, reserve_ctas: int = 0) -> None:
-    _check(load_library().coop_set_schedule(_h(ctx), seed & 0xFFFFFFFFFFFFFFFF, float(p_kill), float(p_fork),
-                                            int(reserve_ctas)), "coop_set_schedule")
+def coop_set_schedule(ctx, seed: int, p_kill: float, p_fork: float) -> None:
+    _check(load_library().coop_set_schedule(_h(ctx), seed & 0xFFFFFFFFFFFFFFFF, float(p_kill), float(p_fork)),
+           "coop_set_schedule")
 
 
 def coop_set_timeout(ctx, timeout_us: int) -> None:

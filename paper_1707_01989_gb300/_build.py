@@ -34,8 +34,9 @@ def needs_build() -> bool:
 
 
 def build_command(out: str) -> list:
-    return [nvcc_path(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-            "-o", out, *SOURCES]
+    # -rdc + cudadevrt: the kernels launch their own forked CTAs (device-side launches)
+    return [nvcc_path(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-rdc=true", "-shared", "-Xcompiler", "-fPIC",
+            "-o", out, *SOURCES, "-lcudadevrt"]
 
 
 def build_library(force: bool = False, verbose: bool = False) -> str:

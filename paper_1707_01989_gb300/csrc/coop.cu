@@ -84,28 +84,69 @@ __device__ __forceinline__ uint32_t find_entry(const uint32_t *qo, uint32_t F, u
   return lo + 31u - (uint32_t)__clz(b);
 }
 
-// Warp-aggregated enqueue of (v, first column, degree) for the lanes with push = true.
-__device__ __forceinline__ void enqueue(const Params &p, uint32_t out, bool push, uint32_t v, uint32_t rs,
-                                        uint32_t deg, unsigned lane) {
-  const unsigned pm = __ballot_sync(kFull, push);
-  if (pm == 0u) return;
-  uint32_t x = push ? deg : 0u;
+// Per-warp staging of enqueued vertices in shared memory: lanes append (v, first column,
+// degree) without atomics; once 32 or more are staged the warp publishes them with ONE
+// 64-bit atomicAdd on the output queue's (vertices << 32 | edges) counter, a two-pass
+// warp scan of the degrees for their edge-space offsets, and coalesced stores.
+constexpr int kStage = 64;
+struct WarpStage {
+  uint32_t v[kStage];
+  uint32_t rs[kStage];
+  uint32_t deg[kStage];
+};
+
+template <int MODE>
+__device__ __forceinline__ void stage_flush(const Params &p, uint32_t out, WarpStage &b, uint32_t n, unsigned lane) {
+  __syncwarp();
+  const uint32_t d0 = lane < n ? b.deg[lane] : 0u;
+  const uint32_t d1 = lane + 32u < n ? b.deg[lane + 32u] : 0u;
+  uint32_t s0 = d0, s1 = d1;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(kFull, x, o);
-    if ((int)lane >= o) x += y;
+    const uint32_t y0 = __shfl_up_sync(kFull, s0, o);
+    const uint32_t y1 = __shfl_up_sync(kFull, s1, o);
+    if ((int)lane >= o) {
+      s0 += y0;
+      s1 += y1;
+    }
   }
-  const uint32_t total = __shfl_sync(kFull, x, 31);
+  const uint32_t t0 = __shfl_sync(kFull, s0, 31);
+  const uint32_t total = t0 + __shfl_sync(kFull, s1, 31);
   unsigned long long base = 0ull;
-  if (lane == 0)
-    base = atomicAdd(&p.ctl->qctr[out], ((unsigned long long)__popc(pm) << 32) | (unsigned long long)total);
+  if (lane == 0) base = atomicAdd(&p.ctl->qctr[out], ((unsigned long long)n << 32) | (unsigned long long)total);
   base = __shfl_sync(kFull, base, 0);
+  const uint32_t bc = (uint32_t)(base >> 32), be = (uint32_t)base;
+  uint32_t *qo = out ? p.qo[1] : p.qo[0];
+  uint32_t *qs = out ? p.qs[1] : p.qs[0];
+  uint32_t *qv = out ? p.qv[1] : p.qv[0];
+  if (lane < n) {
+    qo[bc + lane] = be + s0 - d0;
+    qs[bc + lane] = b.rs[lane];
+    if (MODE == MODE_SSSP) qv[bc + lane] = b.v[lane];
+  }
+  if (lane + 32u < n) {
+    qo[bc + 32u + lane] = be + t0 + s1 - d1;
+    qs[bc + 32u + lane] = b.rs[lane + 32u];
+    if (MODE == MODE_SSSP) qv[bc + 32u + lane] = b.v[lane + 32u];
+  }
+  __syncwarp();
+}
+
+template <int MODE>
+__device__ __forceinline__ void stage_push(const Params &p, uint32_t out, WarpStage &b, uint32_t &n, bool push,
+                                           uint32_t v, uint32_t rs, uint32_t deg, unsigned lane) {
+  const unsigned pm = __ballot_sync(kFull, push);
+  if (pm == 0u) return;
   if (push) {
-    const uint32_t slot = (uint32_t)(base >> 32) + (uint32_t)__popc(pm & lanemask_lt());
-    const uint32_t off = (uint32_t)base + x - deg;
-    (out ? p.qo[1] : p.qo[0])[slot] = off;
-    (out ? p.qs[1] : p.qs[0])[slot] = rs;
-    (out ? p.qv[1] : p.qv[0])[slot] = v;
+    const uint32_t at = n + (uint32_t)__popc(pm & lanemask_lt());
+    b.v[at] = v;
+    b.rs[at] = rs;
+    b.deg[at] = deg;
+  }
+  n += (uint32_t)__popc(pm);
+  if (n >= 32u) {
+    stage_flush<MODE>(p, out, b, n, lane);
+    n = 0u;
   }
 }
 
@@ -118,12 +159,17 @@ __device__ __forceinline__ bool row_of(const Params &p, uint32_t v, uint32_t &rs
   return true;
 }
 
-// Expand this warp's share of the interval's edge space.
-template <int MODE>
-__device__ void expand(const Params &p, const Interval &iv, int32_t id) {
+constexpr int kUnroll = 4;  // 32-edge chunks a warp has in flight per iteration
+
+// Expand this warp's share of the interval's edge space, kUnroll chunks at a time:
+// first the index arithmetic of all chunks (window slides, source entry per lane),
+// then all column loads, then all state loads, so every lane keeps kUnroll
+// independent memory chains in flight.
+template <int MODE, int NW>
+__device__ void expand(const Params &p, const Interval &iv, int32_t id, WarpStage &stage) {
   const unsigned lane = threadIdx.x & 31u;
-  const uint64_t GW = (uint64_t)iv.M * kWarps;
-  const uint64_t gw = (uint64_t)id * kWarps + (threadIdx.x >> 5);
+  const uint64_t GW = (uint64_t)iv.M * NW;
+  const uint64_t gw = (uint64_t)id * NW + (threadIdx.x >> 5);
   const uint32_t Etot = iv.edges;
   const uint32_t E0 = (uint32_t)((uint64_t)Etot * gw / GW);
   const uint32_t E1 = (uint32_t)((uint64_t)Etot * (gw + 1u) / GW);
@@ -142,90 +188,174 @@ __device__ void expand(const Params &p, const Interval &iv, int32_t id) {
   load_entry<MODE>(p, qo, qs, qv, F, Etot, wb + lane, w);
   bool bad = false;
   bool ovf = false;
+  uint32_t staged = 0u;
 
-  for (uint32_t c = E0; c < E1; c += 32u) {
-    // slide the window so that lane 0 holds the entry containing edge c
-    const unsigned ended = __ballot_sync(kFull, w.end <= c);
-    if (ended) {
-      const unsigned n = (unsigned)__popc(ended);
-      wb += n;
-      const unsigned srcl = (lane + n) & 31u;
-      Window s;
-      s.off = __shfl_sync(kFull, w.off, srcl);
-      s.end = __shfl_sync(kFull, w.end, srcl);
-      s.start = __shfl_sync(kFull, w.start, srcl);
-      if (MODE == MODE_SSSP) {
-        s.u = __shfl_sync(kFull, w.u, srcl);
-        s.du = __shfl_sync(kFull, w.du, srcl);
+  for (uint32_t c = E0; c < E1; c += 32u * kUnroll) {
+    uint32_t pos[kUnroll], du[kUnroll];
+    bool val[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint32_t cu = c + 32u * (uint32_t)u;
+      val[u] = false;
+      pos[u] = 0u;
+      du[u] = 0u;
+      if (cu >= E1) continue;  // warp-uniform
+      // slide the window so that lane 0 holds the entry containing edge cu
+      const unsigned ended = __ballot_sync(kFull, w.end <= cu);
+      if (ended) {
+        const unsigned n = (unsigned)__popc(ended);
+        wb += n;
+        const unsigned srcl = (lane + n) & 31u;
+        Window s;
+        s.off = __shfl_sync(kFull, w.off, srcl);
+        s.end = __shfl_sync(kFull, w.end, srcl);
+        s.start = __shfl_sync(kFull, w.start, srcl);
+        if (MODE == MODE_SSSP) {
+          s.u = __shfl_sync(kFull, w.u, srcl);
+          s.du = __shfl_sync(kFull, w.du, srcl);
+        }
+        if (lane + n < 32u) w = s;
+        else load_entry<MODE>(p, qo, qs, qv, F, Etot, wb + lane, w);
       }
-      if (lane + n < 32u) w = s;
-      else load_entry<MODE>(p, qo, qs, qv, F, Etot, wb + lane, w);
+      // entries starting strictly inside [cu, cu+32) -> source entry of each lane's edge
+      const uint32_t rel = w.off - cu;
+      const unsigned bit = (lane != 0u && rel < 32u) ? (1u << rel) : 0u;
+      const unsigned bits = __reduce_or_sync(kFull, bit);
+      const unsigned idx = (unsigned)__popc(bits & lm_le);
+      const uint32_t s0 = __shfl_sync(kFull, w.start, idx);
+      const uint32_t o0 = __shfl_sync(kFull, w.off, idx);
+      if (MODE == MODE_SSSP) du[u] = __shfl_sync(kFull, w.du, idx);
+      const uint32_t e = cu + lane;
+      val[u] = e < E1;
+      pos[u] = s0 + (e - o0);
     }
-    // entries starting strictly inside [c, c+32) -> source entry of each lane's edge
-    const uint32_t rel = w.off - c;
-    const unsigned bit = (lane != 0u && rel < 32u) ? (1u << rel) : 0u;
-    const unsigned bits = __reduce_or_sync(kFull, bit);
-    const unsigned idx = (unsigned)__popc(bits & lm_le);
-    const uint32_t s0 = __shfl_sync(kFull, w.start, idx);
-    const uint32_t o0 = __shfl_sync(kFull, w.off, idx);
-    uint32_t du = 0u;
-    if (MODE == MODE_SSSP) du = __shfl_sync(kFull, w.du, idx);
-    const uint32_t e = c + lane;
-    const bool valid = e < E1;
-    const uint32_t pos = s0 + (e - o0);
-
-    bool push = false;
-    uint32_t v = 0u, rs = 0u, deg = 0u;
-    if (valid) {
-      v = (uint32_t)__ldg(p.col + pos);
-      if (v >= V) {
-        bad = true;
-      } else if (MODE == MODE_BFS) {
-        const uint32_t m = 1u << (v & 31u);
-        uint32_t *word = p.visited + (v >> 5);
-        if ((*word & m) == 0u && (atomicOr(word, m) & m) == 0u) {
-          p.level[v] = (int32_t)next_level;
-          if (row_of(p, v, rs, deg)) push = deg > 0u;
+    uint32_t vv[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) vv[u] = val[u] ? (uint32_t)__ldg(p.col + pos[u]) : 0xFFFFFFFFu;
+    if (MODE == MODE_BFS) {
+      uint32_t word[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        if (val[u] && vv[u] >= V) {
+          bad = true;
+          val[u] = false;
+        }
+        word[u] = val[u] ? *(p.visited + (vv[u] >> 5)) : 0xFFFFFFFFu;
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const uint32_t m = 1u << (vv[u] & 31u);
+        bool claim = false;
+        if (val[u] && (word[u] & m) == 0u) claim = (atomicOr(p.visited + (vv[u] >> 5), m) & m) == 0u;
+        uint32_t rs = 0u, deg = 0u;
+        bool push = false;
+        if (claim) {
+          p.level[vv[u]] = (int32_t)next_level;
+          if (row_of(p, vv[u], rs, deg)) push = deg > 0u;
           else bad = true;
         }
-      } else {
-        const uint64_t nd64 = (uint64_t)du + (uint64_t)__ldg(p.w + pos);
-        if (nd64 >= 0xFFFFFFFFull) {
-          ovf = true;
-        } else {
-          const uint32_t nd = (uint32_t)nd64;
-          uint32_t *dv = p.dist + v;
-          if (nd < *(volatile uint32_t *)dv && nd < atomicMin(dv, nd)) {
-            const uint32_t tag = next_level + 1u;  // stamp of "queued for the next round"
-            uint32_t *sv = p.stamp + v;
-            if (*(volatile uint32_t *)sv != tag && atomicExch(sv, tag) != tag) {
-              if (row_of(p, v, rs, deg)) push = deg > 0u;
-              else bad = true;
+        stage_push<MODE>(p, out, stage, staged, push, vv[u], rs, deg, lane);
+      }
+    } else {
+      uint32_t wt[kUnroll], dv[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) wt[u] = val[u] ? __ldg(p.w + pos[u]) : 0u;
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        if (val[u] && vv[u] >= V) {
+          bad = true;
+          val[u] = false;
+        }
+        dv[u] = val[u] ? *(volatile const uint32_t *)(p.dist + vv[u]) : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        bool push = false;
+        uint32_t rs = 0u, deg = 0u;
+        if (val[u]) {
+          const uint64_t nd64 = (uint64_t)du[u] + (uint64_t)wt[u];
+          if (nd64 >= 0xFFFFFFFFull) {
+            ovf = true;
+          } else {
+            const uint32_t nd = (uint32_t)nd64;
+            if (nd < dv[u] && nd < atomicMin(p.dist + vv[u], nd)) {
+              const uint32_t tag = next_level + 1u;  // stamp of "queued for the next round"
+              uint32_t *sv = p.stamp + vv[u];
+              if (*(volatile uint32_t *)sv != tag && atomicExch(sv, tag) != tag) {
+                if (row_of(p, vv[u], rs, deg)) push = deg > 0u;
+                else bad = true;
+              }
             }
           }
         }
+        stage_push<MODE>(p, out, stage, staged, push, vv[u], rs, deg, lane);
       }
     }
-    enqueue(p, out, push, v, rs, deg, lane);
   }
+  if (staged) stage_flush<MODE>(p, out, stage, staged, lane);
   if (bad) raise_err(p, ERR_GRAPH);
   if (ovf) p.ctl->ovf = 1u;
 }
 
-template <int MODE>
-__device__ __forceinline__ void worker_loop(const Params &p, CtaShared &cs) {
+template <int MODE, int NW>
+__global__ void __launch_bounds__((NW + 1) * 32, 1) coop_traverse(const __grid_constant__ Params p, int join);
+
+}  // namespace
+
+namespace coopdev {
+// request_fork seen from the scheduler: n new CTAs of this very kernel, launched from
+// the device into a fire-and-forget stream.  They register on arrival and are admitted
+// at the next resizing barrier; the parent grid completes only after they have left.
+template <int MODE, int NW>
+__device__ void spawn_forks(const Params &p, uint32_t n) {
+  coop_traverse<MODE, NW><<<n, (NW + 1) * 32, kReserveSmem, cudaStreamFireAndForget>>>(p, 1);
+}
+}  // namespace coopdev
+
+namespace {
+
+// The scheduler warp of the master CTA (the scheduler side of query() and fork):
+// mirrors the host's cumulative kill requests into L2 for the barrier's release path and
+// launches the CTAs the host gives back.  Runs until the traversal is over or the
+// master's own workers have left.
+template <int MODE, int NW>
+__device__ __forceinline__ void scheduler_warp(const Params &p, const volatile int32_t *workers_left) {
+  Ctl *c = p.ctl;
+  uint32_t kills_seen = p.kill_base, forks_seen = p.fork_base;
+  for (;;) {
+    const uint32_t r = ld_sys(&p.mbox->kill_req);
+    if (r != kills_seen) {
+      st_relaxed(&c->kill_req_mirror, r);
+      kills_seen = r;
+    }
+    const uint32_t f = ld_sys(&p.mbox->fork_req);
+    if ((int32_t)(f - forks_seen) > 0) {
+      const uint32_t n = f - forks_seen;
+      forks_seen = f;
+      atomicAdd(&c->launched_total, n);
+      spawn_forks<MODE, NW>(p, n);
+    }
+    if (ld_relaxed(&c->done) != 0u || ld_relaxed(&c->err) != 0u || *workers_left != 0) return;
+    __nanosleep(500);
+  }
+}
+
+template <int MODE, int NW>
+__device__ __forceinline__ void worker_loop(const Params &p, CtaShared &cs, WarpStage *stages) {
+  WarpStage &stage = stages[threadIdx.x >> 5];
   for (;;) {
     const Interval iv = cs.iv;
     const int32_t id = cs.id;
     if (iv.done || id >= iv.M) return;  // finished, or left through offer_kill
-    if (MODE != MODE_BARRIER) expand<MODE>(p, iv, id);
-    if (!resizing_barrier<MODE>(p, cs)) return;
+    if (MODE != MODE_BARRIER) expand<MODE, NW>(p, iv, id, stage);
+    if (!resizing_barrier<MODE, NW>(p, cs)) return;
   }
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(kBlock, 1) coop_traverse(const __grid_constant__ Params p, int join) {
+template <int MODE, int NW>
+__global__ void __launch_bounds__((NW + 1) * 32, 1) coop_traverse(const __grid_constant__ Params p, int join) {
   __shared__ CtaShared cs;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];  // per-warp enqueue staging (+ SM reservation)
   if (threadIdx.x == 0) {
     bool active;
     if (!join && blockIdx.x == 0) {
@@ -241,11 +371,11 @@ __global__ void __launch_bounds__(kBlock, 1) coop_traverse(const __grid_constant
   }
   __syncthreads();
   if (cs.exit) return;
-  if (threadIdx.x >= kWorkers) {
-    if (p.coop && cs.id == 0 && threadIdx.x == kWorkers) poller(p, &cs.workers_left);
+  if (threadIdx.x >= NW * 32) {
+    if (p.coop && cs.id == 0 && threadIdx.x == NW * 32) scheduler_warp<MODE, NW>(p, &cs.workers_left);
     return;
   }
-  worker_loop<MODE>(p, cs);
+  worker_loop<MODE, NW>(p, cs, reinterpret_cast<WarpStage *>(dyn_smem));
   if (threadIdx.x == 0) *(volatile int32_t *)&cs.workers_left = 1;
 }
 
@@ -311,10 +441,10 @@ __global__ void __launch_bounds__(1024) coop_saxpy_kernel(int64_t n, float a, co
 
 struct coop_ctx {
   int device = 0;
+  int nw = kDefaultWorkerWarps;  // worker warps per traversal CTA
   int N = 0;
   int sm_count = 0;
-  cudaStream_t join_stream = nullptr;
-  cudaEvent_t ev_init = nullptr, ev_done = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_done = nullptr;
   cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;  // kernel timing (optional)
   bool timing = false;
   Mailbox *mbox = nullptr;    // host view
@@ -329,11 +459,10 @@ struct coop_ctx {
   bool launched = false;
   Params cur{};
   int cur_mode = MODE_BFS;
-  uint32_t kill_req = 0, served = 0, returned = 0;
+  uint32_t kill_req = 0, served = 0, returned = 0, fork_req = 0;
   int64_t timeout_us = 2000000;
   uint64_t sched_seed = 0;
   double p_kill = 0.0, p_fork = 0.0;
-  int reserve = 0;
   double gather_us_max = 0.0;
 };
 
@@ -367,12 +496,13 @@ inline void store_release(uint32_t *p, uint32_t v) { __atomic_store_n(p, v, __AT
 
 bool running(coop_ctx *c) { return c->launched && cudaEventQuery(c->ev_done) == cudaErrorNotReady; }
 
-// Fold a finished run's kills into the host's books and grant outstanding requests.
+// Fold the CTAs the device has surrendered into the host's books (always), and once no
+// traversal is in flight grant every still-outstanding request at once.
 void finalize_locked(coop_ctx *c) {
-  if (running(c)) return;
-  (void)cudaGetLastError();
   const uint32_t f = load_acquire(&c->mbox->freed);
   if ((int32_t)(f - c->served) > 0) c->served = f;
+  if (running(c)) return;
+  (void)cudaGetLastError();
   if ((int32_t)(c->kill_req - c->served) > 0) c->served = c->kill_req;  // idle grant
   store_release(&c->mbox->freed, c->served);
 }
@@ -380,7 +510,7 @@ void finalize_locked(coop_ctx *c) {
 coop_status ensure_scratch(coop_ctx *c, int64_t V) {
   if (V <= c->cap_V) return COOP_OK;
   if (c->scratch) {
-    cudaStreamSynchronize(c->join_stream);
+    if (c->launched) cudaEventSynchronize(c->ev_done);
     cudaFree(c->scratch);
     c->scratch = nullptr;
     c->cap_V = 0;
@@ -420,6 +550,25 @@ coop_status check_graph(const coop_csr *g, int32_t source) {
   return COOP_OK;
 }
 
+// The traversal kernel instantiations: worker warps NW in {31, 23, 15} (+ 1 poller warp).
+template <int MODE>
+const void *traverse_fn(int nw) {
+  switch (nw) {
+    case 31: return (const void *)coop_traverse<MODE, 31>;
+    case 23: return (const void *)coop_traverse<MODE, 23>;
+    default: return (const void *)coop_traverse<MODE, 15>;
+  }
+}
+
+template <int MODE>
+void launch_traverse(int nw, int grid, const Params &p, int join, cudaStream_t s) {
+  switch (nw) {
+    case 31: coop_traverse<MODE, 31><<<grid, 32 * 32, kReserveSmem, s>>>(p, join); break;
+    case 23: coop_traverse<MODE, 23><<<grid, 24 * 32, kReserveSmem, s>>>(p, join); break;
+    default: coop_traverse<MODE, 15><<<grid, 16 * 32, kReserveSmem, s>>>(p, join); break;
+  }
+}
+
 template <int MODE>
 coop_status launch_run(coop_ctx *c, const coop_csr *g, const uint32_t *w, int32_t source, int32_t *level,
                        uint32_t *dist, cudaStream_t stream, coop_stats *stats, bool coop, int32_t n_barriers,
@@ -457,6 +606,7 @@ coop_status launch_run(coop_ctx *c, const coop_csr *g, const uint32_t *w, int32_
     p.N = c->N;
     p.launched = (uint32_t)launched;
     p.kill_base = c->served;
+    p.fork_base = c->fork_req;
     p.timeout_ns = (uint64_t)std::max<int64_t>(c->timeout_us, 1) * 1000ull;
     p.sched_seed = c->sched_seed;
     p.p_kill = (uint32_t)std::min(4294967295.0, std::max(0.0, c->p_kill) * 4294967296.0);
@@ -471,18 +621,12 @@ coop_status launch_run(coop_ctx *c, const coop_csr *g, const uint32_t *w, int32_
     c->mbox->status = 0;
     store_release(&c->mbox->freed, c->served);
     store_release(&c->mbox->kill_req, c->kill_req);
+    store_release(&c->mbox->fork_req, c->fork_req);
 
-    cudaStreamWaitEvent(stream, c->ev_join, 0);  // fork launches of earlier runs are gone
     coop_init_kernel<MODE><<<c->sm_count * 4, 512, 0, stream>>>(p);
-    cudaEventRecord(c->ev_init, stream);
     if (c->timing) cudaEventRecord(c->ev_t0, stream);
-    coop_traverse<MODE><<<launched, kBlock, kReserveSmem, stream>>>(p, 0);
+    launch_traverse<MODE>(c->nw, launched, p, 0, stream);
     if (c->timing) cudaEventRecord(c->ev_t1, stream);
-    if (coop && p.sched_on && c->reserve > 0) {
-      cudaStreamWaitEvent(c->join_stream, c->ev_init, 0);
-      coop_traverse<MODE><<<c->reserve, kBlock, kReserveSmem, c->join_stream>>>(p, 1);
-    }
-    cudaEventRecord(c->ev_join, c->join_stream);
     cudaEventRecord(c->ev_done, stream);
     if (cuda_failed(cudaGetLastError(), "traversal launch")) return COOP_ECUDA;
     c->cur = p;
@@ -495,11 +639,6 @@ coop_status launch_run(coop_ctx *c, const coop_csr *g, const uint32_t *w, int32_
     return coop_get_stats(c, stats);
   }
   return COOP_OK;
-}
-
-template <int MODE>
-void launch_join(coop_ctx *c, int n) {
-  coop_traverse<MODE><<<n, kBlock, kReserveSmem, c->join_stream>>>(c->cur, 1);
 }
 
 }  // namespace
@@ -525,7 +664,13 @@ const char *coop_status_string(coop_status s) {
 coop_status coop_init(int device, int max_ctas, int threads_per_cta, coop_ctx **out) {
   if (!out) return COOP_EINVAL;
   *out = nullptr;
-  if (max_ctas < 0 || (threads_per_cta != 0 && threads_per_cta != kWorkers)) return COOP_EINVAL;
+  if (max_ctas < 0) return COOP_EINVAL;
+  int nw = 0;
+  if (threads_per_cta == 0) nw = kDefaultWorkerWarps;
+  else if (threads_per_cta == 31 * 32 || threads_per_cta == 23 * 32 || threads_per_cta == 15 * 32)
+    nw = threads_per_cta / 32;
+  else
+    return COOP_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
     (void)cudaGetLastError();
@@ -541,15 +686,15 @@ coop_status coop_init(int device, int max_ctas, int threads_per_cta, coop_ctx **
   };
   if (cuda_failed(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device), "sm count"))
     return fail(COOP_ECUDA);
-  const void *kernels[] = {(const void *)coop_traverse<MODE_BFS>, (const void *)coop_traverse<MODE_SSSP>,
-                           (const void *)coop_traverse<MODE_BARRIER>};
+  c->nw = nw;
+  const void *kernels[] = {traverse_fn<MODE_BFS>(nw), traverse_fn<MODE_SSSP>(nw), traverse_fn<MODE_BARRIER>(nw)};
   int per_sm = 1 << 30;
   for (const void *k : kernels) {
     if (cuda_failed(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kReserveSmem),
                     "set traversal smem"))
       return fail(COOP_ECUDA);
     int nb = 0;
-    if (cuda_failed(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBlock, kReserveSmem), "occupancy"))
+    if (cuda_failed(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, (nw + 1) * 32, kReserveSmem), "occupancy"))
       return fail(COOP_ECUDA);
     per_sm = std::min(per_sm, nb);
   }
@@ -561,14 +706,23 @@ coop_status coop_init(int device, int max_ctas, int threads_per_cta, coop_ctx **
     snprintf(g_last_error, sizeof(g_last_error), "traversal kernel cannot be resident (%d per SM)", per_sm);
     return fail(COOP_ECUDA);
   }
+  // Load every kernel now.  With lazy module loading the first launch of a kernel
+  // waits for kernels already running, so a co-runner launched for the first time
+  // while a traversal runs would not start until the traversal ended.
+  {
+    const void *all[] = {traverse_fn<MODE_BFS>(nw), traverse_fn<MODE_SSSP>(nw), traverse_fn<MODE_BARRIER>(nw),
+                         (const void *)coop_init_kernel<MODE_BFS>, (const void *)coop_init_kernel<MODE_SSSP>,
+                         (const void *)coop_init_kernel<MODE_BARRIER>, (const void *)coop_saxpy_kernel};
+    for (const void *k : all) {
+      cudaFuncAttributes fa;
+      if (cuda_failed(cudaFuncGetAttributes(&fa, k), "kernel attributes")) return fail(COOP_ECUDA);
+    }
+    coop_saxpy_kernel<<<1, 1024, kCorunnerSmem>>>(0, 0.f, nullptr, nullptr);  // n = 0: no work
+    if (cuda_failed(cudaGetLastError(), "co-runner warm-up")) return fail(COOP_ECUDA);
+  }
   const int cap = std::min(per_sm * c->sm_count, kMaxCtas);
   c->N = max_ctas == 0 ? cap : std::min(max_ctas, cap);
-  if (cuda_failed(cudaStreamCreateWithFlags(&c->join_stream, cudaStreamNonBlocking), "join stream"))
-    return fail(COOP_ECUDA);
-  if (cuda_failed(cudaEventCreateWithFlags(&c->ev_init, cudaEventDisableTiming), "event") ||
-      cuda_failed(cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming), "event") ||
-      cuda_failed(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "event"))
-    return fail(COOP_ECUDA);
+  if (cuda_failed(cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming), "event")) return fail(COOP_ECUDA);
   if (cuda_failed(cudaHostAlloc((void **)&c->mbox, sizeof(Mailbox), cudaHostAllocMapped | cudaHostAllocPortable),
                   "mailbox"))
     return fail(COOP_ENOMEM);
@@ -577,7 +731,6 @@ coop_status coop_init(int device, int max_ctas, int threads_per_cta, coop_ctx **
     return fail(COOP_ECUDA);
   if (cuda_failed(cudaMalloc((void **)&c->ctl, sizeof(Ctl)), "control block")) return fail(COOP_ENOMEM);
   if (cuda_failed(cudaMemset(c->ctl, 0, sizeof(Ctl)), "control block memset")) return fail(COOP_ECUDA);
-  cudaEventRecord(c->ev_join, c->join_stream);
   if (cuda_failed(cudaDeviceSynchronize(), "init sync")) return fail(COOP_ECUDA);
   *out = c;
   return COOP_OK;
@@ -587,16 +740,12 @@ coop_status coop_destroy(coop_ctx *c) {
   if (!c) return COOP_OK;
   DeviceGuard guard(c->device);
   if (c->ev_done && c->launched) cudaEventSynchronize(c->ev_done);
-  if (c->join_stream) cudaStreamSynchronize(c->join_stream);
   if (c->scratch) cudaFree(c->scratch);
   if (c->ctl) cudaFree(c->ctl);
   if (c->mbox) cudaFreeHost(c->mbox);
-  if (c->ev_init) cudaEventDestroy(c->ev_init);
   if (c->ev_done) cudaEventDestroy(c->ev_done);
-  if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->ev_t0) cudaEventDestroy(c->ev_t0);
   if (c->ev_t1) cudaEventDestroy(c->ev_t1);
-  if (c->join_stream) cudaStreamDestroy(c->join_stream);
   (void)cudaGetLastError();
   delete c;
   return COOP_OK;
@@ -696,19 +845,13 @@ coop_status coop_release(coop_ctx *c, int n) {
   DeviceGuard guard(c->device);
   std::lock_guard<std::mutex> lk(c->mu);
   finalize_locked(c);
-  const uint32_t f = load_acquire(&c->mbox->freed);
-  if ((int32_t)(f - c->served) > 0) c->served = f;
   const int held = (int)(c->served - c->returned);
   if (n > held) return COOP_EINVAL;
   c->returned += (uint32_t)n;
   if (running(c)) {
-    switch (c->cur_mode) {
-      case MODE_BFS: launch_join<MODE_BFS>(c, n); break;
-      case MODE_SSSP: launch_join<MODE_SSSP>(c, n); break;
-      default: launch_join<MODE_BARRIER>(c, n); break;
-    }
-    cudaEventRecord(c->ev_join, c->join_stream);
-    if (cuda_failed(cudaGetLastError(), "fork launch")) return COOP_ECUDA;
+    // the running kernel's scheduler warp launches the n CTAs; they join at a barrier
+    c->fork_req += (uint32_t)n;
+    store_release(&c->mbox->fork_req, c->fork_req);
   }
   return COOP_OK;
 }
@@ -717,7 +860,6 @@ coop_status coop_sync(coop_ctx *c) {
   if (!c) return COOP_EINVAL;
   DeviceGuard guard(c->device);
   if (c->launched && cudaEventSynchronize(c->ev_done) != cudaSuccess) return COOP_ECUDA;
-  if (cudaStreamSynchronize(c->join_stream) != cudaSuccess) return COOP_ECUDA;
   std::lock_guard<std::mutex> lk(c->mu);
   finalize_locked(c);
   const int32_t e = __atomic_load_n(&c->mbox->err, __ATOMIC_ACQUIRE);
@@ -739,6 +881,7 @@ coop_status coop_get_stats(coop_ctx *c, coop_stats *s) {
   s->min_active = m->min_active;
   s->max_active = m->max_active;
   s->initial_active = m->initial_active;
+  s->ctas_launched = m->ctas_launched;
   s->edges_scanned = (int64_t)m->edges_scanned;
   s->frontier_total = (int64_t)m->frontier_total;
   s->gather_us_max = c->gather_us_max;
@@ -767,15 +910,12 @@ coop_status coop_get_resize_log(coop_ctx *c, int32_t *out, int cap, int *n) {
   return COOP_OK;
 }
 
-coop_status coop_set_schedule(coop_ctx *c, uint64_t seed, double p_kill, double p_fork, int reserve_ctas) {
-  if (!c || p_kill < 0.0 || p_kill > 1.0 || p_fork < 0.0 || p_fork > 1.0 || reserve_ctas < 0 ||
-      reserve_ctas > kMaxCtas)
-    return COOP_EINVAL;
+coop_status coop_set_schedule(coop_ctx *c, uint64_t seed, double p_kill, double p_fork) {
+  if (!c || p_kill < 0.0 || p_kill > 1.0 || p_fork < 0.0 || p_fork > 1.0) return COOP_EINVAL;
   std::lock_guard<std::mutex> lk(c->mu);
   c->sched_seed = seed;
   c->p_kill = p_kill;
   c->p_fork = p_fork;
-  c->reserve = reserve_ctas;
   return COOP_OK;
 }
 
@@ -805,7 +945,7 @@ coop_status coop_query(coop_ctx *c, int *max_ctas, int *threads_per_cta, int *sm
   std::lock_guard<std::mutex> lk(c->mu);
   finalize_locked(c);
   if (max_ctas) *max_ctas = c->N;
-  if (threads_per_cta) *threads_per_cta = kWorkers;
+  if (threads_per_cta) *threads_per_cta = c->nw * 32;
   if (sm_count) *sm_count = c->sm_count;
   if (lent) *lent = (int)(c->served - c->returned);
   return COOP_OK;

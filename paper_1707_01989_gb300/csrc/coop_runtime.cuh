@@ -14,16 +14,19 @@
 //    the scheduler for W, (4) broadcasts the next interval (the transmitted state) and
 //    the new M; (5) the CTAs with logical ids >= M' leave.  Fork happens before kill,
 //    so ids [0, min(M, M')-1] are untouched (Sec. 3.1).
-//  * request_fork via join-on-arrival: every CTA other than the master first registers
-//    (takes a ticket) and waits for the release that admits it; a CTA counts towards M
-//    only after admission, so a launched-but-not-resident CTA never holds a barrier up.
+//  * request_fork via join-on-arrival: new CTAs come from device-side (fire-and-forget)
+//    launches of the same kernel made by the running kernel itself -- by the scheduler
+//    warp when the host returns SMs, by the releaser under a forced schedule.  Every CTA
+//    other than the master first registers (takes a ticket) and waits for the release
+//    that admits it; a CTA counts towards M only after admission, so a launched but not
+//    yet resident CTA never holds a barrier up.
 //  * transmit: the interval record (level, input queue, frontier size) is written by
 //    the releaser before the release and read by every CTA after it; joiners read the
 //    same record, which is "thread 0 of workgroup 0's" transmitted state since those
 //    values are uniform across the kernel (the observation of Appendix B).
-//  * the scheduler side of query(): a poller warp in the master CTA mirrors the host's
+//  * the scheduler side of query(): a scheduler warp in the master CTA mirrors the host's
 //    request counter (mapped pinned memory, system scope) into device memory, so the
-//    barrier's release path reads only L2.
+//    barrier's release path reads only L2, and launches the CTAs the host gives back.
 //
 // Every spin-wait reads %globaltimer and gives up after the context's limit, setting a
 // sticky error that all other waits observe; nothing here can wait forever.
@@ -32,9 +35,9 @@
 
 namespace coopdev {
 
-constexpr int kWorkers = 992;               // worker threads per CTA (31 warps)
-constexpr int kWarps = kWorkers / 32;
-constexpr int kBlock = kWorkers + 32;       // + one scheduler (poller) warp = 1024
+// Worker warps per CTA is a template parameter NW of the kernels (31, 23 or 15); every
+// CTA has NW worker warps plus one scheduler (poller) warp, (NW + 1) * 32 <= 1024 threads.
+constexpr int kDefaultWorkerWarps = 31;
 constexpr int kMaxCtas = 2048;              // admission slot table; N <= kMaxCtas
 constexpr int kLogCap = 4096;               // resize-log records per run
 constexpr int kReserveSmem = 116 * 1024;    // dynamic smem of a traversal CTA
@@ -87,6 +90,8 @@ struct Ctl {
   uint32_t done;             // set by the final release
   uint32_t ovf;              // SSSP distance overflow seen
   uint32_t pad_h[27];
+  alignas(128) uint32_t launched_total;  // CTAs launched for this run (main grid + forks)
+  uint32_t pad_l[31];
   // releaser-private bookkeeping (serialised by the barrier)
   alignas(128) uint32_t admitted;
   uint32_t killed_host;
@@ -101,12 +106,14 @@ struct Ctl {
 // Host <-> device mailbox in mapped pinned host memory.
 struct alignas(128) Mailbox {
   uint32_t kill_req;  // host -> device: cumulative CTAs requested by the scheduler
-  uint32_t pad0[31];
+  uint32_t fork_req;  // host -> device: cumulative CTAs the scheduler gave back
+  uint32_t pad0[30];
   uint32_t freed;     // device -> host: cumulative requested CTAs that have left
   int32_t err;        // device -> host: sticky error of the current run
   uint32_t run_done;  // device -> host: id of the last run that finished
   uint32_t pad1[29];
   int32_t levels, barriers, kills, forks, min_active, max_active, initial_active, status;
+  int32_t ctas_launched, pad2;
   unsigned long long edges_scanned, frontier_total;
 };
 
@@ -131,6 +138,7 @@ struct Params {
   int32_t N;
   uint32_t launched;   // CTAs in the main launch (the master waits for them at entry)
   uint32_t kill_base;  // scheduler requests already served when the run started
+  uint32_t fork_base;  // host fork grants already consumed when the run started
   uint64_t timeout_ns;
   uint64_t sched_seed;
   uint32_t p_kill;     // schedule: kill probability * 2^32 (0 = never)
@@ -197,8 +205,9 @@ __device__ __forceinline__ void st_sys(uint32_t *p, uint32_t v) {
 __device__ __forceinline__ void st_sys64(unsigned long long *p, uint64_t v) {
   asm volatile("st.relaxed.sys.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+template <int NW>
 __device__ __forceinline__ void workers_sync() {
-  asm volatile("bar.sync 1, %0;" ::"n"(kWorkers) : "memory");
+  asm volatile("bar.sync 1, %0;" ::"n"(NW * 32) : "memory");
 }
 __device__ __forceinline__ unsigned lanemask_le() {
   unsigned m;
@@ -229,14 +238,14 @@ __device__ __forceinline__ Interval read_iv(const Ctl *c) {
 }
 
 // ---------------------------------------------------------------- errors / stats
-__device__ __noinline__ void raise_err(const Params &p, int code) {
+__device__ __forceinline__ void raise_err(const Params &p, int code) {
   if (atomicCAS(&p.ctl->err, 0u, (uint32_t)code) == 0u) {
     st_sys((uint32_t *)&p.mbox->err, (uint32_t)code);
     __threadfence_system();
   }
 }
 
-__device__ __noinline__ void publish_stats(const Params &p, int status) {
+__device__ __forceinline__ void publish_stats(const Params &p, int status) {
   Ctl *c = p.ctl;
   Mailbox *m = p.mbox;
   st_sys((uint32_t *)&m->levels, (uint32_t)c->iv.level);
@@ -247,6 +256,7 @@ __device__ __noinline__ void publish_stats(const Params &p, int status) {
   st_sys((uint32_t *)&m->max_active, (uint32_t)c->max_active);
   st_sys((uint32_t *)&m->initial_active, (uint32_t)c->initial_active);
   st_sys((uint32_t *)&m->status, (uint32_t)status);
+  st_sys((uint32_t *)&m->ctas_launched, ld_relaxed(&c->launched_total));
   st_sys64(&m->edges_scanned, c->edges_scanned);
   st_sys64(&m->frontier_total, c->frontier_total);
   __threadfence_system();
@@ -262,7 +272,7 @@ __device__ __forceinline__ uint64_t slot_pack(uint32_t epoch, uint32_t killed, u
 }
 
 // Wait until the epoch word differs from `e` (a release happened).  false on error/timeout.
-__device__ __noinline__ bool wait_release(const Params &p, uint32_t e) {
+__device__ __forceinline__ bool wait_release(const Params &p, uint32_t e) {
   Ctl *c = p.ctl;
   const uint64_t t0 = gtime();
   for (uint32_t spin = 0;; ++spin) {
@@ -279,7 +289,7 @@ __device__ __noinline__ bool wait_release(const Params &p, uint32_t e) {
 }
 
 // Wait until the epoch word reaches `e` (a joiner waiting for its admission release).
-__device__ __noinline__ bool wait_epoch_at_least(const Params &p, uint32_t e) {
+__device__ __forceinline__ bool wait_epoch_at_least(const Params &p, uint32_t e) {
   Ctl *c = p.ctl;
   const uint64_t t0 = gtime();
   for (uint32_t spin = 0;; ++spin) {
@@ -299,8 +309,11 @@ __device__ __noinline__ bool wait_epoch_at_least(const Params &p, uint32_t e) {
 // Runs in thread 0 of the last CTA to arrive, while every other active CTA waits.
 // Computes the next interval from the output queue, admits joiners (fork), asks the
 // scheduler for W (query), kills from the top, logs the resize and publishes.
-template <int MODE>
-__device__ __noinline__ Interval release_step(const Params &p, const Interval cur) {
+template <int MODE, int NW>
+__device__ void spawn_forks(const Params &p, uint32_t n);
+
+template <int MODE, int NW>
+__device__ __forceinline__ Interval release_step(const Params &p, const Interval cur) {
   Ctl *c = p.ctl;
   Interval nxt = cur;
   nxt.epoch = cur.epoch + 1u;
@@ -330,10 +343,17 @@ __device__ __noinline__ Interval release_step(const Params &p, const Interval cu
     k = (int32_t)min((uint32_t)(p.N - M), R - A);
     int32_t Ws = 0;
     if (p.sched_on) {
+      // forced schedule: the scheduler grants up to kcap in [0, N-M] new CTAs (spawned
+      // now, admitted when they arrive) and accepts W in [0, M-1] offer_kills
       const uint64_t r = mix64(p.sched_seed ^ mix64((uint64_t)(c->barriers + 1)));
       const uint64_t r2 = mix64(r);
       const int32_t kcap = ((uint32_t)(r >> 32) < p.p_fork) ? (int32_t)(r2 % (uint64_t)(p.N - M + 1)) : 0;
-      k = min(k, kcap);
+      const int32_t pending = (int32_t)(ld_relaxed(&c->launched_total) - 1u - A);
+      const int32_t spawn = kcap - pending;
+      if (spawn > 0) {
+        atomicAdd(&c->launched_total, (uint32_t)spawn);
+        spawn_forks<MODE, NW>(p, (uint32_t)spawn);
+      }
       if ((uint32_t)r < p.p_kill) Ws = (int32_t)((r2 >> 32) % (uint64_t)M);
     }
     // (3) query: W = CTAs the scheduler still needs (never CTA 0)
@@ -379,16 +399,16 @@ __device__ __noinline__ Interval release_step(const Params &p, const Interval cu
 
 // The resizing global barrier, called by all worker threads of an active CTA.
 // Returns false when the run is aborting (error or timeout).
-template <int MODE>
+template <int MODE, int NW>
 __device__ __forceinline__ bool resizing_barrier(const Params &p, CtaShared &cs) {
-  workers_sync();  // the CTA's work for the interval is done
+  workers_sync<NW>();  // the CTA's work for the interval is done
   if (threadIdx.x == 0) {
     Ctl *c = p.ctl;
     const Interval cur = cs.iv;
     const uint32_t old = atom_add_acq_rel(&c->arrive.v, 1u);
     bool ok = true;
     if (old == (uint32_t)(cur.M - 1) + p.extra_wait) {
-      const Interval nxt = release_step<MODE>(p, cur);
+      const Interval nxt = release_step<MODE, NW>(p, cur);
       st_relaxed(&c->arrive.v, 0u);
       st_release(&c->epoch.v, cur.epoch + 1u);
       cs.iv = nxt;
@@ -398,14 +418,14 @@ __device__ __forceinline__ bool resizing_barrier(const Params &p, CtaShared &cs)
     }
     cs.ok = ok ? 1 : 0;
   }
-  workers_sync();
+  workers_sync<NW>();
   return cs.ok != 0;
 }
 
 // ---------------------------------------------------------------- entry
 // A CTA that is not the master registers and waits for a release that admits it
 // (request_fork seen from the forked side).  Returns false if it should leave.
-__device__ __noinline__ bool join_enter(const Params &p, CtaShared &cs) {
+__device__ __forceinline__ bool join_enter(const Params &p, CtaShared &cs) {
   Ctl *c = p.ctl;
   if (ld_relaxed(&c->run) != p.run || ld_relaxed(&c->done) != 0u || ld_relaxed(&c->err) != 0u) return false;
   const uint32_t t = atomicAdd(&c->join_ticket.v, 1u);
@@ -428,7 +448,7 @@ __device__ __noinline__ bool join_enter(const Params &p, CtaShared &cs) {
 }
 
 // Non-cooperative baseline entry: fixed id = blockIdx.x, wait for the master's start.
-__device__ __noinline__ bool plain_enter(const Params &p, CtaShared &cs) {
+__device__ __forceinline__ bool plain_enter(const Params &p, CtaShared &cs) {
   Ctl *c = p.ctl;
   if (!wait_epoch_at_least(p, 1u)) return false;
   cs.iv = read_iv(c);
@@ -439,7 +459,7 @@ __device__ __noinline__ bool plain_enter(const Params &p, CtaShared &cs) {
 // The master (block 0 of the main launch, logical id 0) seeds the frontier, waits
 // briefly for its launch to register, admits them and opens interval 1 (level 0).
 template <int MODE>
-__device__ __noinline__ void master_enter(const Params &p, CtaShared &cs) {
+__device__ __forceinline__ void master_enter(const Params &p, CtaShared &cs) {
   Ctl *c = p.ctl;
   uint32_t count = 0u, edges = 0u;
   if (MODE == MODE_BARRIER) {
@@ -487,6 +507,7 @@ __device__ __noinline__ void master_enter(const Params &p, CtaShared &cs) {
   iv.epoch = 1u;
   iv.pad = 0u;
   c->admitted = (uint32_t)k;
+  st_relaxed(&c->launched_total, p.coop ? p.launched : gridDim.x);
   c->initial_active = iv.M;
   c->min_active = iv.M;
   c->max_active = iv.M;
@@ -501,22 +522,6 @@ __device__ __noinline__ void master_enter(const Params &p, CtaShared &cs) {
   st_release(&c->epoch.v, 1u);
   cs.iv = iv;
   cs.id = 0;
-}
-
-// The scheduler side of query(): mirror the host's request counter into L2.  Runs in
-// the master CTA until the run is over or the master's own workers have left.
-__device__ __noinline__ void poller(const Params &p, const volatile int32_t *workers_left) {
-  Ctl *c = p.ctl;
-  uint32_t last = p.kill_base;
-  for (;;) {
-    const uint32_t r = ld_sys(&p.mbox->kill_req);
-    if (r != last) {
-      st_relaxed(&c->kill_req_mirror, r);
-      last = r;
-    }
-    if (ld_relaxed(&c->done) != 0u || ld_relaxed(&c->err) != 0u || *workers_left != 0) return;
-    __nanosleep(500);
-  }
 }
 
 }  // namespace coopdev
