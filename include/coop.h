@@ -200,6 +200,32 @@ coop_status coop_saxpy(int n_ctas, int64_t n, float a, const float *d_x, float *
                        coop_stream stream);
 
 /*
+ * Allocation-free BFS.  The paper has no counterpart: this is a deployment variant of
+ * coop_bfs for callers that must not allocate device memory -- processes that reserve
+ * their whole device-memory budget up front through their own pool, code running inside
+ * an allocator's or memory pool's callbacks (which must not re-enter the allocator), and
+ * latency-critical loops that cannot take cudaMalloc's implicit device synchronisation
+ * (which would also wait for any running traversal).  It needs no context and calls no
+ * allocating routine: its scratch (control block, mailbox, visited bitmap, frontier
+ * queues) is one static device array compiled into libcoop.so, about 25 MB, which every
+ * GPU that loads the library holds until the process exits.
+ *
+ *  - Limit: graphs of at most 2^20 (1,048,576) vertices; larger ones are rejected with
+ *    COOP_EINVAL (coop_last_cuda_error() names the limit) before any GPU work.
+ *  - Inputs and outputs as coop_bfs: g (device CSR), source, d_levels (int32[V], device);
+ *    d_status (nullable, device int32) receives the run's coop_status when it finishes.
+ *  - Asynchronous on `stream`.  It runs with every CTA that fits (no host scheduler:
+ *    coop_request_resources / coop_release do not apply).
+ *  - The first call on a device (the current device) looks up the array's device address
+ *    and sets kernel attributes; make that first call before any stream capture.
+ *  - Every call shares the one array, which keeps the last call's contents; each call
+ *    clears what must start at zero.  Calls whose work overlaps on the GPU race with each
+ *    other and corrupt each other's results: order them (one stream, or events).
+ */
+coop_status coop_bfs_noalloc(const coop_csr *g, int32_t source, int32_t *d_levels, int32_t *d_status,
+                             coop_stream stream);
+
+/*
  * Text of the last failing CUDA runtime call made by this library on the calling
  * thread ("" if none): which step failed, the CUDA error name and its description.
  * Useful after COOP_ECUDA; the string stays valid until the thread's next failure.

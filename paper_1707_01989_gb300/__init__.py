@@ -21,7 +21,7 @@ __all__ = [
     "CoopError", "CoopUnavailable", "Stats", "CSR", "coop_init", "coop_destroy", "coop_bfs", "coop_sssp",
     "coop_request_resources", "coop_release", "coop_sync", "coop_get_stats", "coop_get_resize_log",
     "coop_set_schedule", "coop_set_timeout", "coop_set_timing", "coop_query", "coop_bfs_baseline", "coop_sssp_baseline",
-    "coop_barrier_bench", "coop_saxpy", "coop_status_string", "coop_last_cuda_error", "library_path", "load_library",
+    "coop_barrier_bench", "coop_saxpy", "coop_bfs_noalloc", "coop_status_string", "coop_last_cuda_error", "library_path", "load_library",
 ]
 
 COOP_OK, COOP_EINVAL, COOP_ENOMEM, COOP_ECUDA = 0, -1, -2, -3
@@ -100,6 +100,7 @@ def load_library():
                 "coop_query": [vp, ip, ip, ip, ip],
                 "coop_barrier_bench": [vp, i32, i32, vp, sp],
                 "coop_saxpy": [ctypes.c_int, i64, ctypes.c_float, vp, vp, vp],
+                "coop_bfs_noalloc": [cp, i32, vp, vp, vp],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -301,6 +302,14 @@ def coop_query(ctx) -> dict:
     _check(load_library().coop_query(_h(ctx), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)),
            "coop_query")
     return {"max_ctas": a.value, "threads_per_cta": b.value, "sm_count": c.value, "lent": d.value}
+
+
+def coop_bfs_noalloc(g: CSR, source: int, levels, status=None, stream=None) -> None:
+    """Allocation-free BFS (static scratch, at most 2^20 vertices); asynchronous."""
+    st = load_library().coop_bfs_noalloc(ctypes.byref(g), int(source),
+                                         _ptr(levels, "torch.int32", g.num_vertices, "levels"),
+                                         _ptr(status, "torch.int32", 1, "status"), _stream(stream))
+    _check(st, "coop_bfs_noalloc")
 
 
 def coop_saxpy(n_ctas: int, a: float, x, y, stream=None) -> None:

@@ -964,3 +964,121 @@ coop_status coop_saxpy(int n_ctas, int64_t n, float a, const float *d_x, float *
 }
 
 }  // extern "C"
+
+// ===================================================================== allocation-free BFS
+//
+// coop_bfs_noalloc runs the same cooperative BFS kernels as coop_bfs, but takes its
+// scratch (control block, mailbox, visited bitmap, both frontier queues) from one static
+// device array compiled into this library instead of memory allocated at run time.  It
+// serves callers that must not allocate device memory: processes that reserve their
+// whole device-memory budget up front through their own pool, code running inside an
+// allocator's or a memory pool's callbacks (which must not re-enter the allocator), and
+// latency-critical loops that cannot take cudaMalloc's implicit device synchronisation
+// (which would also wait for any traversal still running).
+
+namespace {
+
+constexpr int64_t kNoAllocMaxVertices = (int64_t)1 << 20;
+constexpr size_t na_align(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t kNaMboxOff = na_align(sizeof(Ctl));
+constexpr size_t kNaBitmapOff = kNaMboxOff + na_align(sizeof(Mailbox));
+constexpr size_t kNaQueueOff = kNaBitmapOff + na_align((size_t)(kNoAllocMaxVertices + 31) / 32 * 4);
+constexpr size_t kNaQueueBytes = na_align((size_t)kNoAllocMaxVertices * 4);
+constexpr size_t kNaBytes = kNaQueueOff + 6 * kNaQueueBytes;  // about 25 MB
+
+// The scratch of coop_bfs_noalloc.  Every GPU that loads the library holds it until the
+// process exits.  In host code this name is only a stand-in: the device address comes
+// from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+// Final status of an allocation-free run: its sticky error, else its published status,
+// else (the run never published) a timeout.
+__global__ void coop_noalloc_status_kernel(const Mailbox *m, uint32_t run, int32_t *out) {
+  const int32_t e = *(volatile const int32_t *)&m->err;
+  const uint32_t finished = *(volatile const uint32_t *)&m->run_done;
+  *out = e != 0 ? e : (finished == run ? *(volatile const int32_t *)&m->status : (int32_t)COOP_ETIMEOUT);
+}
+
+struct NoAllocDevice {
+  bool ready = false;
+  unsigned char *base = nullptr;  // device address of g_noalloc_scratch on this device
+  int ctas = 0;
+  int sms = 0;
+  uint32_t run = 0;
+};
+constexpr int kNoAllocDevices = 64;
+std::mutex g_noalloc_mu;
+NoAllocDevice g_noalloc[kNoAllocDevices];
+
+}  // namespace
+
+extern "C" coop_status coop_bfs_noalloc(const coop_csr *g, int32_t source, int32_t *d_levels, int32_t *d_status,
+                                        coop_stream stream) {
+  if (!d_levels) return COOP_EINVAL;
+  const coop_status st = check_graph(g, source);
+  if (st != COOP_OK) return st;
+  if ((int64_t)g->num_vertices > kNoAllocMaxVertices) {
+    snprintf(g_last_error, sizeof(g_last_error),
+             "coop_bfs_noalloc: %d vertices exceed the static scratch limit of %lld vertices", g->num_vertices,
+             (long long)kNoAllocMaxVertices);
+    return COOP_EINVAL;
+  }
+  int dev = -1;
+  if (cuda_failed(cudaGetDevice(&dev), "current device")) return COOP_ECUDA;
+  if (dev < 0 || dev >= kNoAllocDevices) return COOP_EINVAL;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  NoAllocDevice &d = g_noalloc[dev];
+  if (!d.ready) {
+    // one-time set-up on this device (the current one): the scratch's device address,
+    // the kernel's shared-memory attribute and the CTA count.  Nothing is allocated.
+    void *ptr = nullptr;
+    if (cuda_failed(cudaGetSymbolAddress(&ptr, g_noalloc_scratch), "scratch symbol address")) return COOP_ECUDA;
+    const void *k = traverse_fn<MODE_BFS>(kDefaultWorkerWarps);
+    if (cuda_failed(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kReserveSmem),
+                    "set traversal smem"))
+      return COOP_ECUDA;
+    int nb = 0, sms = 0;
+    if (cuda_failed(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "sm count") ||
+        cuda_failed(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, (kDefaultWorkerWarps + 1) * 32,
+                                                                  kReserveSmem),
+                    "occupancy"))
+      return COOP_ECUDA;
+    if (nb < 1) {
+      snprintf(g_last_error, sizeof(g_last_error), "traversal kernel cannot be resident (%d per SM)", nb);
+      return COOP_ECUDA;
+    }
+    d.base = static_cast<unsigned char *>(ptr);
+    d.ctas = std::min(nb * sms, kMaxCtas);
+    d.sms = sms;
+    d.ready = true;
+  }
+  Params p{};
+  p.row_off = g->row_off;
+  p.col = g->col;
+  p.V = g->num_vertices;
+  p.E = (uint32_t)g->num_edges;
+  p.level = d_levels;
+  p.ctl = reinterpret_cast<Ctl *>(d.base);
+  p.mbox = reinterpret_cast<Mailbox *>(d.base + kNaMboxOff);
+  p.visited = reinterpret_cast<uint32_t *>(d.base + kNaBitmapOff);
+  for (int i = 0; i < 2; ++i) {
+    p.qo[i] = reinterpret_cast<uint32_t *>(d.base + kNaQueueOff + (size_t)(3 * i + 0) * kNaQueueBytes);
+    p.qs[i] = reinterpret_cast<uint32_t *>(d.base + kNaQueueOff + (size_t)(3 * i + 1) * kNaQueueBytes);
+    p.qv[i] = reinterpret_cast<uint32_t *>(d.base + kNaQueueOff + (size_t)(3 * i + 2) * kNaQueueBytes);
+  }
+  p.src = source;
+  p.N = d.ctas;
+  p.launched = (uint32_t)d.ctas;
+  p.timeout_ns = 2000000000ull;
+  p.run = ++d.run;
+  p.coop = 1u;
+  cudaStream_t s = (cudaStream_t)stream;
+  // The array keeps the previous call's contents: clear the mailbox (scheduler requests,
+  // error, statistics) here; the init kernel clears the control block and the bitmap.
+  if (cuda_failed(cudaMemsetAsync(p.mbox, 0, sizeof(Mailbox), s), "clear mailbox")) return COOP_ECUDA;
+  coop_init_kernel<MODE_BFS><<<d.sms * 4, 512, 0, s>>>(p);
+  launch_traverse<MODE_BFS>(kDefaultWorkerWarps, d.ctas, p, 0, s);
+  if (d_status) coop_noalloc_status_kernel<<<1, 1, 0, s>>>(p.mbox, p.run, d_status);
+  if (cuda_failed(cudaGetLastError(), "allocation-free launch")) return COOP_ECUDA;
+  return COOP_OK;
+}
