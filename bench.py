@@ -47,7 +47,10 @@ WORKLOADS = {
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the persistent kernel, per
 # workload, from the ncu captures summarised in profiles/; an entry is used only while
 # the kernel sources still have the digest it was taken on (otherwise null).
-TRAFFIC = {}
+TRAFFIC = {
+    "rmat20-sssp": {"sources_sha": "dca17530c2105feb", "bytes": 425997312},
+    "rmat22-bfs": {"sources_sha": "dca17530c2105feb", "bytes": 399318272},
+}
 
 
 def sources_sha() -> str:
@@ -369,6 +372,102 @@ def main():
     return 0
 
 
+def random_schedules(coop, ctx, csr, src, lv, ref, stream, es, seeds=(0, 1, 2, 3)):
+    """R-MAT 22 BFS under seeded random kill/fork schedules: bit-exact flag and throughput."""
+    import numpy as np
+    res = []
+    for seed in seeds:
+        coop.coop_set_schedule(ctx, seed, 0.3, 0.5)
+        t0 = time.perf_counter()
+        st = coop.coop_bfs(ctx, csr, src, lv, stream=stream, stats=True)
+        dt = time.perf_counter() - t0
+        res.append({"seed": seed, "bit_exact": bool(np.array_equal(lv.cpu().numpy(), ref)), "kills": st.kills,
+                    "forks": st.forks, "min_active": st.min_active, "kernel_us": round(st.kernel_us, 1),
+                    "gteps_kernel": round(es / (st.kernel_us / 1e6) / 1e9, 2), "host_ms": round(dt * 1e3, 2)})
+    coop.coop_set_schedule(ctx, 0, 0.0, 0.0)
+    return res
+
+
+def corunner(coop, ctx, dev, csr, src, lv, stream, period_s=1.0 / 60.0, duration_s=1.5):
+    """Cooperative multitasking: a periodic fp32 saxpy over 64 MB (x and y, 16.7 ms period)
+    that claims half the SMs from back-to-back R-MAT 22 BFS traversals.
+
+    Latency of one co-runner job = host time from coop_request_resources (the gather) to
+    the saxpy's completion; solo = the same path with no traversal in flight.  The
+    traversals' throughput with and without the co-runner gives the cooperative kernel's
+    slowdown (the analogue of the paper's Sec. 5.4 measurements)."""
+    import torch
+    N = coop.coop_query(ctx)["max_ctas"]
+    half = N // 2
+    n_el = 16 * 1024 * 1024
+    x = torch.rand(n_el, device=dev)
+    y = torch.rand(n_el, device=dev)
+    cs = torch.cuda.Stream(device=dev, priority=-1)
+    for _ in range(3):
+        coop.coop_saxpy(half, 2.0, x, y, stream=cs)
+    cs.synchronize()
+
+    def job():
+        t0 = time.perf_counter()
+        got = coop.coop_request_resources(ctx, half, timeout_us=2_000_000)
+        t1 = time.perf_counter()
+        coop.coop_saxpy(half, 2.0, x, y, stream=cs)
+        cs.synchronize()
+        t2 = time.perf_counter()
+        coop.coop_release(ctx, got)
+        return (t2 - t0) * 1e3, (t1 - t0) * 1e3
+
+    solo = [job()[0] for _ in range(40)]
+    # traversal throughput alone
+    coop.coop_bfs(ctx, csr, src, lv, stream=stream)
+    stream.synchronize()
+    t0 = time.perf_counter()
+    n_alone = 0
+    while time.perf_counter() - t0 < 0.5:
+        coop.coop_bfs(ctx, csr, src, lv, stream=stream)
+        n_alone += 1
+    stream.synchronize()
+    per_alone = (time.perf_counter() - t0) / n_alone
+    # traversals back to back while the co-runner ticks every period
+    lat, gat = [], []
+    stop = threading.Event()
+
+    def ticker():
+        nxt = time.perf_counter()
+        while not stop.is_set():
+            l, g = job()
+            lat.append(l)
+            gat.append(g)
+            nxt += period_s
+            time.sleep(max(0.0, nxt - time.perf_counter()))
+
+    th = threading.Thread(target=ticker)
+    t0 = time.perf_counter()
+    th.start()
+    n_co = 0
+    while time.perf_counter() - t0 < duration_s:
+        coop.coop_bfs(ctx, csr, src, lv, stream=stream)
+        n_co += 1
+    stream.synchronize()
+    per_co = (time.perf_counter() - t0) / n_co
+    stop.set()
+    th.join()
+    coop.coop_sync(ctx)
+
+    def pct(v, q):
+        v = sorted(v)
+        return round(v[min(len(v) - 1, int(round(q * (len(v) - 1))))], 4)
+
+    return {"period_ms": round(period_s * 1e3, 2), "claimed_ctas": half, "of_ctas": N, "jobs": len(lat),
+            "latency_ms_p50": pct(lat, 0.5), "latency_ms_p99": pct(lat, 0.99),
+            "solo_ms_p50": pct(solo, 0.5), "solo_ms_p99": pct(solo, 0.99),
+            "p99_vs_solo": round(pct(lat, 0.99) / pct(solo, 0.99), 3),
+            "gather_ms_p50": pct(gat, 0.5), "gather_ms_p99": pct(gat, 0.99),
+            "deadline_ms": 2.0, "deadline_met_frac": round(sum(l <= 2.0 for l in lat) / max(1, len(lat)), 4),
+            "traversal_ms_alone": round(per_alone * 1e3, 4), "traversal_ms_corun": round(per_co * 1e3, 4),
+            "coop_slowdown": round(per_co / per_alone, 4)}
+
+
 def secondary(coop, ctx, dev, stream, flush, args):
     """BFS on R-MAT 22, grid BFS, barrier latency and the non-cooperative baseline ratio."""
     import numpy as np
@@ -414,6 +513,8 @@ def secondary(coop, ctx, dev, stream, flush, args):
                          "ms": round(ms, 4), "kernel_us": round(kus, 2), "gteps": round(es / (ms / 1e3) / 1e9, 3),
                          "hbm_frac": round(B / (kus / 1e6) / 1e9 / hbm, 4),
                          "baseline_kernel_us": round(kusb, 2), "coop_overhead": round(kus / kusb, 4)}
+    out["bfs_rmat22_schedules"] = random_schedules(coop, ctx, csr, src, lv, lvh, stream, es)
+    out["corunner"] = corunner(coop, ctx, dev, csr, src, lv, stream)
     del ro, col, lv
     # grid 256x256 BFS: barrier-latency bound
     g = gg.grid(256, 256)

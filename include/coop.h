@@ -140,9 +140,11 @@ coop_status coop_sync(coop_ctx *ctx);
 coop_status coop_get_stats(coop_ctx *ctx, coop_stats *stats);
 
 /*
- * Resize log of the last completed traversal: one record per resizing barrier that
- * changed M, four int32 each {M_before, k_forked, W_killed, M_after}, in order.
- * Writes min(cap, available) records to out (host memory) and the number written to *n.
+ * Resize log of the last completed traversal (the runtime's trace): one record per
+ * resizing barrier that admitted, removed or launched CTAs, in order, seven int32 each:
+ * {barrier index, microseconds since the run started, M_before, k_forked, W_killed,
+ * M_after, CTAs launched there by a forced schedule}.  Writes min(cap, available) records
+ * to out (host memory, 7*cap int32) and the number written to *n.  At most 4096 records.
  */
 coop_status coop_get_resize_log(coop_ctx *ctx, int32_t *out, int cap, int *n);
 

@@ -276,12 +276,15 @@ def coop_get_stats(ctx, ok=(COOP_OK,)) -> Stats:
     return s
 
 
+LOG_FIELDS = ("barrier", "t_us", "m_before", "k_forked", "w_killed", "m_after", "spawned")
+
+
 def coop_get_resize_log(ctx, cap: int = 4096):
-    """List of (M_before, k_forked, W_killed, M_after) records of the last traversal."""
-    buf = (ctypes.c_int32 * (4 * cap))()
+    """Resize records of the last traversal: tuples in the order of LOG_FIELDS."""
+    buf = (ctypes.c_int32 * (7 * cap))()
     n = ctypes.c_int(0)
     _check(load_library().coop_get_resize_log(_h(ctx), buf, cap, ctypes.byref(n)), "coop_get_resize_log")
-    return [tuple(buf[4 * i: 4 * i + 4]) for i in range(n.value)]
+    return [tuple(buf[7 * i: 7 * i + 7]) for i in range(n.value)]
 
 
 def coop_set_schedule(ctx, seed: int, p_kill: float, p_fork: float) -> None:

@@ -454,7 +454,8 @@ struct coop_ctx {
   int64_t cap_V = 0;
   uint32_t *visited = nullptr, *stamp = nullptr;
   uint32_t *qv[2] = {nullptr, nullptr}, *qs[2] = {nullptr, nullptr}, *qo[2] = {nullptr, nullptr};
-  std::mutex mu;
+  std::mutex mu;         // host bookkeeping (kill/fork counters, run state)
+  std::mutex launch_mu;  // serialises traversal launches
   uint32_t run = 0;
   bool launched = false;
   Params cur{};
@@ -574,9 +575,12 @@ coop_status launch_run(coop_ctx *c, const coop_csr *g, const uint32_t *w, int32_
                        uint32_t *dist, cudaStream_t stream, coop_stats *stats, bool coop, int32_t n_barriers,
                        int32_t extra_wait) {
   DeviceGuard guard(c->device);
+  // One traversal at a time.  The wait for the previous one happens without holding the
+  // state lock, so the scheduler's calls from other threads never queue behind a GPU wait.
+  std::lock_guard<std::mutex> launch_lk(c->launch_mu);
+  if (c->launched) cudaEventSynchronize(c->ev_done);
   {
     std::lock_guard<std::mutex> lk(c->mu);
-    if (c->launched && running(c)) cudaEventSynchronize(c->ev_done);  // one traversal at a time
     finalize_locked(c);
     const int64_t V = g ? g->num_vertices : 0;
     coop_status st = ensure_scratch(c, std::max<int64_t>(V, 1));
@@ -904,8 +908,22 @@ coop_status coop_get_resize_log(coop_ctx *c, int32_t *out, int cap, int *n) {
   uint32_t ln = 0;
   if (cudaMemcpy(&ln, &c->ctl->log_n, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return COOP_ECUDA;
   const int take = std::min<int>((int)std::min<uint32_t>(ln, (uint32_t)kLogCap), cap);
-  if (take > 0 && cudaMemcpy(out, c->ctl->log, sizeof(LogRec) * (size_t)take, cudaMemcpyDeviceToHost) != cudaSuccess)
-    return COOP_ECUDA;
+  if (take > 0) {
+    LogRec *tmp = new LogRec[take];
+    const cudaError_t e = cudaMemcpy(tmp, c->ctl->log, sizeof(LogRec) * (size_t)take, cudaMemcpyDeviceToHost);
+    for (int i = 0; e == cudaSuccess && i < take; ++i) {
+      int32_t *r = out + 7 * (size_t)i;
+      r[0] = tmp[i].barrier;
+      r[1] = tmp[i].t_us;
+      r[2] = tmp[i].m_before;
+      r[3] = tmp[i].k;
+      r[4] = tmp[i].w;
+      r[5] = tmp[i].m_after;
+      r[6] = tmp[i].spawned;
+    }
+    delete[] tmp;
+    if (cuda_failed(e, "resize log copy")) return COOP_ECUDA;
+  }
   *n = take;
   return COOP_OK;
 }

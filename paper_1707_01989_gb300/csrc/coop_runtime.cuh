@@ -65,8 +65,11 @@ struct Interval {
   uint32_t pad;
 };
 
+// One resize record: barrier index, microseconds since the run started, the active count
+// before, CTAs admitted (fork), CTAs leaving (kill), the active count after, and CTAs
+// launched at this barrier by a forced schedule.
 struct LogRec {
-  int32_t m_before, k, w, m_after;
+  int32_t barrier, t_us, m_before, k, w, m_after, spawned, pad;
 };
 
 struct alignas(128) Word {
@@ -97,8 +100,9 @@ struct Ctl {
   uint32_t killed_host;
   int32_t barriers, kills, forks, min_active, max_active, initial_active;
   unsigned long long edges_scanned, frontier_total;
+  unsigned long long t_start;  // %globaltimer at the master's entry
   uint32_t log_n;
-  uint32_t pad_b[15];
+  uint32_t pad_b[13];
   alignas(128) unsigned long long slot[kMaxCtas];  // admission records, by ticket % kMaxCtas
   LogRec log[kLogCap];
 };
@@ -335,7 +339,7 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
   nxt.done = (count == 0u || ld_relaxed(&c->err) != 0u) ? 1u : 0u;
 
   const int32_t M = cur.M;
-  int32_t k = 0, W = 0, Wh = 0;
+  int32_t k = 0, W = 0, Wh = 0, spawned = 0;
   uint32_t A = c->admitted;
   if (!nxt.done && p.coop) {
     // (2) fork: admit CTAs that registered and wait, up to N - M
@@ -353,6 +357,7 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
       if (spawn > 0) {
         atomicAdd(&c->launched_total, (uint32_t)spawn);
         spawn_forks<MODE, NW>(p, (uint32_t)spawn);
+        spawned = spawn;
       }
       if ((uint32_t)r < p.p_kill) Ws = (int32_t)((r2 >> 32) % (uint64_t)M);
     }
@@ -383,8 +388,9 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
     c->edges_scanned += edges;
     c->frontier_total += count;
   }
-  if ((k | W) != 0 && c->log_n < (uint32_t)kLogCap) {
-    c->log[c->log_n] = LogRec{M, k, W, Mn};
+  if ((k | W | spawned) != 0 && c->log_n < (uint32_t)kLogCap) {
+    const int32_t t_us = (int32_t)((gtime() - c->t_start) / 1000ull);
+    c->log[c->log_n] = LogRec{c->barriers, t_us, M, k, W, Mn, spawned, 0};
     c->log_n += 1u;
   }
   nxt.M = Mn;
@@ -507,6 +513,7 @@ __device__ __forceinline__ void master_enter(const Params &p, CtaShared &cs) {
   iv.epoch = 1u;
   iv.pad = 0u;
   c->admitted = (uint32_t)k;
+  c->t_start = gtime();
   st_relaxed(&c->launched_total, p.coop ? p.launched : gridDim.x);
   c->initial_active = iv.M;
   c->min_active = iv.M;

@@ -29,12 +29,18 @@ def ctx(cuda_device):
 
 
 def _replay(ctx, st):
-    log = coop.coop_get_resize_log(ctx)
+    """Replay the device's resize log on the semantics model; returns (M_before, k, W, M_after) records."""
+    full = coop.coop_get_resize_log(ctx)
+    log = [r[2:6] for r in full]
     N = coop.coop_query(ctx)["max_ctas"]
     model = replay_resize_log(N, st.initial_active, log)
     assert sum(r[1] for r in log) == st.forks
     assert sum(r[2] for r in log) == st.kills
     assert min([st.initial_active] + [r[3] for r in log]) == st.min_active
+    barriers = [r[0] for r in full]
+    assert barriers == sorted(barriers) and all(1 <= b <= st.barriers for b in barriers)
+    assert [r[1] for r in full] == sorted(r[1] for r in full)  # timestamps are monotone
+    assert sum(r[6] for r in full) + st.initial_active + st.kills >= st.forks  # forks come from launches
     return log, model
 
 
