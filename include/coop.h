@@ -212,8 +212,9 @@ coop_status coop_saxpy(int n_ctas, int64_t n, float a, const float *d_x, float *
  * queues) is one static device array compiled into libcoop.so, about 25 MB, which every
  * GPU that loads the library holds until the process exits.
  *
- *  - Limit: graphs of at most 2^20 (1,048,576) vertices; larger ones are rejected with
- *    COOP_EINVAL (coop_last_cuda_error() names the limit) before any GPU work.
+ *  - Limit: graphs of at most 2^20 (1,048,576) vertices and 2^25 (33,554,432) edges;
+ *    larger ones are rejected with COOP_EINVAL (coop_last_cuda_error() names the limit)
+ *    before any GPU work.
  *  - Inputs and outputs as coop_bfs: g (device CSR), source, d_levels (int32[V], device);
  *    d_status (nullable, device int32) receives the run's coop_status when it finishes.
  *  - Asynchronous on `stream`.  It runs with every CTA that fits (no host scheduler:

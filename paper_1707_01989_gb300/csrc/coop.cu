@@ -65,30 +65,18 @@ __device__ __forceinline__ void load_entry(const Params &p, const uint32_t *qo, 
   }
 }
 
-// Largest i in [0, F) with qo[i] <= x (qo strictly increasing, qo[0] = 0): a 32-ary search.
-__device__ __forceinline__ uint32_t find_entry(const uint32_t *qo, uint32_t F, uint32_t x, unsigned lane) {
-  uint32_t lo = 0u, hi = F;
-  while (hi - lo > 32u) {
-    const uint32_t step = (hi - lo + 31u) / 32u;
-    const uint32_t idx = lo + lane * step;
-    const bool pred = idx < hi && qo[idx] <= x;
-    const unsigned b = __ballot_sync(kFull, pred);
-    const uint32_t L = 31u - (uint32_t)__clz(b);
-    const uint32_t nlo = lo + L * step;
-    hi = min(nlo + step, hi);
-    lo = nlo;
-  }
-  const uint32_t idx = lo + lane;
-  const bool pred = idx < hi && qo[idx] <= x;
-  const unsigned b = __ballot_sync(kFull, pred);
-  return lo + 31u - (uint32_t)__clz(b);
-}
-
 // Per-warp staging of enqueued vertices in shared memory: lanes append (v, first column,
 // degree) without atomics; once 32 or more are staged the warp publishes them with ONE
 // 64-bit atomicAdd on the output queue's (vertices << 32 | edges) counter, a two-pass
 // warp scan of the degrees for their edge-space offsets, and coalesced stores.
 constexpr int kStage = 64;
+
+// Chunk index: for every unit boundary j*kIndexEdges inside an entry's edge range
+// [o, o + d), record the entry's queue slot.
+__device__ __forceinline__ void index_chunks(uint32_t *qx, uint32_t o, uint32_t d, uint32_t slot) {
+  for (uint32_t j = (o + kIndexEdges - 1u) / kIndexEdges; j * kIndexEdges < o + d; ++j) qx[j] = slot;
+}
+
 struct WarpStage {
   uint32_t v[kStage];
   uint32_t rs[kStage];
@@ -119,15 +107,20 @@ __device__ __forceinline__ void stage_flush(const Params &p, uint32_t out, WarpS
   uint32_t *qo = out ? p.qo[1] : p.qo[0];
   uint32_t *qs = out ? p.qs[1] : p.qs[0];
   uint32_t *qv = out ? p.qv[1] : p.qv[0];
+  uint32_t *qx = out ? p.qx[1] : p.qx[0];
   if (lane < n) {
-    qo[bc + lane] = be + s0 - d0;
+    const uint32_t o = be + s0 - d0;
+    qo[bc + lane] = o;
     qs[bc + lane] = b.rs[lane];
     if (MODE == MODE_SSSP) qv[bc + lane] = b.v[lane];
+    index_chunks(qx, o, d0, bc + lane);
   }
   if (lane + 32u < n) {
-    qo[bc + 32u + lane] = be + t0 + s1 - d1;
+    const uint32_t o = be + t0 + s1 - d1;
+    qo[bc + 32u + lane] = o;
     qs[bc + 32u + lane] = b.rs[lane + 32u];
     if (MODE == MODE_SSSP) qv[bc + 32u + lane] = b.v[lane + 32u];
+    index_chunks(qx, o, d1, bc + 32u + lane);
   }
   __syncwarp();
 }
@@ -161,19 +154,16 @@ __device__ __forceinline__ bool row_of(const Params &p, uint32_t v, uint32_t &rs
 
 constexpr int kUnroll = 4;  // 32-edge chunks a warp has in flight per iteration
 
-// Expand this warp's share of the interval's edge space, kUnroll chunks at a time:
-// first the index arithmetic of all chunks (window slides, source entry per lane),
-// then all column loads, then all state loads, so every lane keeps kUnroll
-// independent memory chains in flight.
-template <int MODE, int NW>
-__device__ void expand(const Params &p, const Interval &iv, int32_t id, WarpStage &stage) {
+// Expand edges [c0, c1) of the interval's edge space; entry wb of the input queue holds
+// edge c0.  kUnroll 32-edge groups at a time: first the index arithmetic of all groups
+// (window slides, source entry per lane), then all column loads, then all state loads,
+// so every lane keeps kUnroll independent memory chains in flight.
+template <int MODE>
+__device__ __forceinline__ void expand_range(const Params &p, const Interval &iv, uint32_t c0, uint32_t c1,
+                                             uint32_t wb, WarpStage &stage, uint32_t &staged, bool &bad,
+                                             bool &ovf) {
   const unsigned lane = threadIdx.x & 31u;
-  const uint64_t GW = (uint64_t)iv.M * NW;
-  const uint64_t gw = (uint64_t)id * NW + (threadIdx.x >> 5);
   const uint32_t Etot = iv.edges;
-  const uint32_t E0 = (uint32_t)((uint64_t)Etot * gw / GW);
-  const uint32_t E1 = (uint32_t)((uint64_t)Etot * (gw + 1u) / GW);
-  if (E0 >= E1) return;
   const uint32_t F = iv.count;
   const uint32_t in = iv.sel, out = in ^ 1u;
   const uint32_t *qo = in ? p.qo[1] : p.qo[0];
@@ -182,15 +172,12 @@ __device__ void expand(const Params &p, const Interval &iv, int32_t id, WarpStag
   const unsigned lm_le = lanemask_le();
   const uint32_t next_level = (uint32_t)iv.level + 1u;
   const uint32_t V = (uint32_t)p.V;
+  const uint32_t E1 = c1;
 
-  uint32_t wb = find_entry(qo, F, E0, lane);
   Window w;
   load_entry<MODE>(p, qo, qs, qv, F, Etot, wb + lane, w);
-  bool bad = false;
-  bool ovf = false;
-  uint32_t staged = 0u;
 
-  for (uint32_t c = E0; c < E1; c += 32u * kUnroll) {
+  for (uint32_t c = c0; c < E1; c += 32u * kUnroll) {
     uint32_t pos[kUnroll], du[kUnroll];
     bool val[kUnroll];
 #pragma unroll
@@ -291,6 +278,39 @@ __device__ void expand(const Params &p, const Interval &iv, int32_t id, WarpStag
         stage_push<MODE>(p, out, stage, staged, push, vv[u], rs, deg, lane);
       }
     }
+  }
+}
+
+// Expand this warp's part of the interval.  The edge space is cut into chunks of
+// kIndexEdges * mult edges, mult in [1, kChunkUnitsMax] chosen so that small frontiers
+// still spread over every warp.  A warp's first chunk is fixed by its logical position
+// -- chunk id*NW + warp, Fig. 4's tid/stride split recomputed from the current M -- and
+// further chunks are claimed from one counter, so warps that drew cheap chunks take
+// over the rest.  The enqueue built a chunk index (entry holding each unit's first
+// edge), so a chunk starts without any search.
+template <int MODE, int NW>
+__device__ void expand(const Params &p, const Interval &iv, int32_t id, WarpStage &stage) {
+  const unsigned lane = threadIdx.x & 31u;
+  const uint32_t Etot = iv.edges;
+  const uint32_t GW = (uint32_t)iv.M * NW;
+  const uint32_t units = (Etot + kIndexEdges - 1u) / kIndexEdges;
+  const uint32_t mult = max(1u, min(kChunkUnitsMax, (units + GW - 1u) / GW));
+  const uint32_t csize = kIndexEdges * mult;
+  const uint32_t nchunks = (units + mult - 1u) / mult;
+  uint32_t j = (uint32_t)id * NW + (threadIdx.x >> 5);
+  if (j >= nchunks) return;
+  const uint32_t *qx = iv.sel ? p.qx[1] : p.qx[0];
+  const uint32_t out = iv.sel ^ 1u;
+  uint32_t staged = 0u;
+  bool bad = false, ovf = false;
+  while (j < nchunks) {
+    // claim the next chunk now; the atomic's latency overlaps this chunk's work
+    uint32_t jn = nchunks;
+    if (lane == 0 && GW < nchunks) jn = GW + atomicAdd(&p.ctl->cursor.v, 1u);
+    const uint32_t c0 = j * csize;
+    const uint32_t c1 = min(c0 + csize, Etot);
+    expand_range<MODE>(p, iv, c0, c1, qx[j * mult], stage, staged, bad, ovf);
+    j = __shfl_sync(kFull, jn, 0);
   }
   if (staged) stage_flush<MODE>(p, out, stage, staged, lane);
   if (bad) raise_err(p, ERR_GRAPH);
@@ -451,8 +471,9 @@ struct coop_ctx {
   Mailbox *mbox_d = nullptr;  // device view of the same pinned page
   Ctl *ctl = nullptr;
   void *scratch = nullptr;
-  int64_t cap_V = 0;
+  int64_t cap_V = 0, cap_chunks = 0;
   uint32_t *visited = nullptr, *stamp = nullptr;
+  uint32_t *qx[2] = {nullptr, nullptr};
   uint32_t *qv[2] = {nullptr, nullptr}, *qs[2] = {nullptr, nullptr}, *qo[2] = {nullptr, nullptr};
   std::mutex mu;         // host bookkeeping (kill/fork counters, run state)
   std::mutex launch_mu;  // serialises traversal launches
@@ -508,18 +529,22 @@ void finalize_locked(coop_ctx *c) {
   store_release(&c->mbox->freed, c->served);
 }
 
-coop_status ensure_scratch(coop_ctx *c, int64_t V) {
-  if (V <= c->cap_V) return COOP_OK;
+coop_status ensure_scratch(coop_ctx *c, int64_t V, int64_t E) {
+  const int64_t chunks = E / kIndexEdges + 2;
+  if (V <= c->cap_V && chunks <= c->cap_chunks) return COOP_OK;
   if (c->scratch) {
     if (c->launched) cudaEventSynchronize(c->ev_done);
     cudaFree(c->scratch);
     c->scratch = nullptr;
     c->cap_V = 0;
+    c->cap_chunks = 0;
   }
-  const int64_t cap = std::max<int64_t>(V, 1024);
+  const int64_t cap = std::max<int64_t>(std::max(V, c->cap_V), 1024);
+  const int64_t capx = std::max<int64_t>(chunks, 1024);
   const size_t words = (size_t)(cap + 31) / 32;
   const size_t qbytes = (size_t)cap * 4;
-  const size_t total = words * 4 + qbytes * 7 + 7 * 256;
+  const size_t xbytes = (size_t)capx * 4;
+  const size_t total = words * 4 + qbytes * 7 + xbytes * 2 + 10 * 256;
   char *base = nullptr;
   if (cudaMalloc(&base, total) != cudaSuccess) {
     (void)cudaGetLastError();
@@ -537,9 +562,11 @@ coop_status ensure_scratch(coop_ctx *c, int64_t V) {
     c->qv[i] = take(qbytes);
     c->qs[i] = take(qbytes);
     c->qo[i] = take(qbytes);
+    c->qx[i] = take(xbytes);
   }
   c->scratch = base;
   c->cap_V = cap;
+  c->cap_chunks = capx;
   return COOP_OK;
 }
 
@@ -583,7 +610,7 @@ coop_status launch_run(coop_ctx *c, const coop_csr *g, const uint32_t *w, int32_
     std::lock_guard<std::mutex> lk(c->mu);
     finalize_locked(c);
     const int64_t V = g ? g->num_vertices : 0;
-    coop_status st = ensure_scratch(c, std::max<int64_t>(V, 1));
+    coop_status st = ensure_scratch(c, std::max<int64_t>(V, 1), g ? g->num_edges : 0);
     if (st != COOP_OK) return st;
     const int held = (int)(c->served - c->returned);
     const int launched = coop ? std::max(1, c->N - held) : c->N;
@@ -603,6 +630,7 @@ coop_status launch_run(coop_ctx *c, const coop_csr *g, const uint32_t *w, int32_
       p.qv[i] = c->qv[i];
       p.qs[i] = c->qs[i];
       p.qo[i] = c->qo[i];
+      p.qx[i] = c->qx[i];
     }
     p.ctl = c->ctl;
     p.mbox = c->mbox_d;
@@ -997,12 +1025,15 @@ coop_status coop_saxpy(int n_ctas, int64_t n, float a, const float *d_x, float *
 namespace {
 
 constexpr int64_t kNoAllocMaxVertices = (int64_t)1 << 20;
+constexpr int64_t kNoAllocMaxEdges = (int64_t)1 << 25;
 constexpr size_t na_align(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t kNaMboxOff = na_align(sizeof(Ctl));
 constexpr size_t kNaBitmapOff = kNaMboxOff + na_align(sizeof(Mailbox));
 constexpr size_t kNaQueueOff = kNaBitmapOff + na_align((size_t)(kNoAllocMaxVertices + 31) / 32 * 4);
 constexpr size_t kNaQueueBytes = na_align((size_t)kNoAllocMaxVertices * 4);
-constexpr size_t kNaBytes = kNaQueueOff + 6 * kNaQueueBytes;  // about 25 MB
+constexpr size_t kNaIndexOff = kNaQueueOff + 6 * kNaQueueBytes;
+constexpr size_t kNaIndexBytes = na_align((size_t)(kNoAllocMaxEdges / kIndexEdges + 2) * 4);
+constexpr size_t kNaBytes = kNaIndexOff + 2 * kNaIndexBytes;  // about 25 MB
 
 // The scratch of coop_bfs_noalloc.  Every GPU that loads the library holds it until the
 // process exits.  In host code this name is only a stand-in: the device address comes
@@ -1035,10 +1066,11 @@ extern "C" coop_status coop_bfs_noalloc(const coop_csr *g, int32_t source, int32
   if (!d_levels) return COOP_EINVAL;
   const coop_status st = check_graph(g, source);
   if (st != COOP_OK) return st;
-  if ((int64_t)g->num_vertices > kNoAllocMaxVertices) {
+  if ((int64_t)g->num_vertices > kNoAllocMaxVertices || g->num_edges > kNoAllocMaxEdges) {
     snprintf(g_last_error, sizeof(g_last_error),
-             "coop_bfs_noalloc: %d vertices exceed the static scratch limit of %lld vertices", g->num_vertices,
-             (long long)kNoAllocMaxVertices);
+             "coop_bfs_noalloc: %d vertices / %lld edges exceed the static scratch limit of %lld vertices and "
+             "%lld edges",
+             g->num_vertices, (long long)g->num_edges, (long long)kNoAllocMaxVertices, (long long)kNoAllocMaxEdges);
     return COOP_EINVAL;
   }
   int dev = -1;
@@ -1083,6 +1115,7 @@ extern "C" coop_status coop_bfs_noalloc(const coop_csr *g, int32_t source, int32
     p.qo[i] = reinterpret_cast<uint32_t *>(d.base + kNaQueueOff + (size_t)(3 * i + 0) * kNaQueueBytes);
     p.qs[i] = reinterpret_cast<uint32_t *>(d.base + kNaQueueOff + (size_t)(3 * i + 1) * kNaQueueBytes);
     p.qv[i] = reinterpret_cast<uint32_t *>(d.base + kNaQueueOff + (size_t)(3 * i + 2) * kNaQueueBytes);
+    p.qx[i] = reinterpret_cast<uint32_t *>(d.base + kNaIndexOff + (size_t)i * kNaIndexBytes);
   }
   p.src = source;
   p.N = d.ctas;

@@ -43,6 +43,8 @@ constexpr int kLogCap = 4096;               // resize-log records per run
 constexpr int kReserveSmem = 116 * 1024;    // dynamic smem of a traversal CTA
 constexpr int kCorunnerSmem = 116 * 1024;   // dynamic smem of a co-runner CTA (sum > SM capacity)
 constexpr uint64_t kEntryGatherNs = 20000;  // master waits this long for its launch to register
+constexpr uint32_t kIndexEdges = 128;       // granularity of the chunk index (edges per unit)
+constexpr uint32_t kChunkUnitsMax = 8;      // a work chunk spans 1..8 units, sized to the frontier
 
 enum Mode : int { MODE_BFS = 0, MODE_SSSP = 1, MODE_BARRIER = 2 };
 
@@ -82,6 +84,7 @@ struct Ctl {
   Word arrive;        // arrivals at the current barrier
   Word epoch;         // release word: bumped by the releaser
   Word join_ticket;   // registrations of CTAs waiting to be admitted
+  Word cursor;        // chunks claimed beyond the first M * NW in the current interval
   alignas(128) unsigned long long qctr[2];  // per queue: (vertices << 32) | edges
   uint64_t pad_q[14];
   alignas(128) Interval iv;  // the current interval (written only by releasers)
@@ -134,6 +137,7 @@ struct Params {
   uint32_t *qv[2];    // frontier queues: vertex id (SSSP)
   uint32_t *qs[2];    //                  first column index (row_off[v])
   uint32_t *qo[2];    //                  exclusive prefix of out-degrees (edge space)
+  uint32_t *qx[2];    // chunk index: entry holding edge j * kIndexEdges, per queue
   Ctl *ctl;
   Mailbox *mbox;
   int32_t V;
@@ -332,6 +336,7 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
     count = (uint32_t)(packed >> 32);
     edges = (uint32_t)packed;
     c->qctr[cur.sel] = 0ull;  // the finished input queue becomes the next output queue
+    c->cursor.v = 0u;
     nxt.sel = out;
   }
   nxt.count = count;
@@ -489,6 +494,7 @@ __device__ __forceinline__ void master_enter(const Params &p, CtaShared &cs) {
         p.qv[0][0] = (uint32_t)s;
         count = 1u;
         edges = (uint32_t)(re - rs);
+        for (uint32_t j = 0; j * kIndexEdges < edges; ++j) p.qx[0][j] = 0u;
       }
     }
   }

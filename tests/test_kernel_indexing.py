@@ -1,12 +1,14 @@
 """Host emulation of the expansion kernel's warp-level index arithmetic.
 
-The persistent kernel maps each lane of a warp to one edge of the frontier's edge
-space with a 32-ary search, a 32-entry window of frontier entries held in registers,
-a ballot over ended entries, a __reduce_or of start bits and a popc over
-lanemask_le.  This test replays exactly that arithmetic in numpy (one vector = one
-warp) over random frontiers and checks that every lane reads column
-start[u] + (e - off[u]) of the entry u that owns edge e, i.e. that no column read can
-leave its row.  It runs before any GPU code does.
+The persistent kernel cuts a frontier's edge space into CHUNK-edge chunks; the
+enqueue records, for every chunk boundary, the queue slot of the entry holding it
+(the chunk index).  A warp expanding a chunk starts a 32-entry window of frontier
+entries at that slot and maps each lane to one edge with a ballot over ended entries,
+a __reduce_or of start bits and a popc over lanemask_le.  This test replays exactly
+that arithmetic in numpy (one vector = one warp) over random frontiers and checks that
+every lane reads column start[u] + (e - off[u]) of the entry u that owns edge e, i.e.
+that no column read can leave its row, and that every edge is expanded exactly once.
+It runs before any GPU code does.
 """
 import numpy as np
 import pytest
@@ -46,10 +48,25 @@ def load(qo, qs, F, Etot, i):
     return MAXU, MAXU, 0
 
 
-def emulate_warp(qo, qs, F, Etot, E0, E1):
+CHUNK = 128  # the index granularity (kIndexEdges); chunks are 1..8 units
+
+
+def index_chunks(qo, degs, nchunks):
+    """The enqueue's chunk index: slot of the entry holding edge j*CHUNK, for every j."""
+    qx = np.full(nchunks, -1, dtype=np.int64)
+    for slot, (o, d) in enumerate(zip(qo, degs)):
+        j = (o + CHUNK - 1) // CHUNK
+        while j * CHUNK < o + d:
+            qx[j] = slot
+            j += 1
+    return qx
+
+
+def emulate_warp(qo, qs, F, Etot, E0, E1, wb=None):
     """Returns a list of (edge, column position) exactly as the kernel computes them."""
     out = []
-    wb = find_entry(qo, F, E0)
+    if wb is None:
+        wb = find_entry(qo, F, E0)
     win = [load(qo, qs, F, Etot, wb + l) for l in range(32)]
     c = E0
     while c < E1:
@@ -74,6 +91,43 @@ def emulate_warp(qo, qs, F, Etot, E0, E1):
                 out.append((e, (s0 + ((e - o0) & FULL)) & FULL))
         c += 32
     return out
+
+
+def check_frontier_chunks(degs, rng):
+    """The chunked scheme: every chunk starts at its indexed entry, no search."""
+    F = len(degs)
+    qo = np.concatenate([[0], np.cumsum(degs)[:-1]]).astype(np.int64)
+    Etot = int(np.sum(degs))
+    gaps = rng.integers(0, 5, size=F)
+    qs = np.concatenate([[0], np.cumsum(degs + gaps)[:-1]]).astype(np.int64)
+    owner = np.repeat(np.arange(F), degs)
+    nchunks = (Etot + CHUNK - 1) // CHUNK
+    qx = index_chunks(qo, degs, nchunks)
+    assert np.all(qx >= 0)
+    assert np.array_equal(qx, owner[np.arange(nchunks) * CHUNK])
+    for mult in (1, 3, 8):
+        seen = np.zeros(Etot, dtype=np.int64)
+        for j in rng.permutation((nchunks + mult - 1) // mult):
+            c0, c1 = j * CHUNK * mult, min((j + 1) * CHUNK * mult, Etot)
+            for e, pos in emulate_warp(qo, qs, F, Etot, c0, c1, wb=int(qx[j * mult])):
+                u = owner[e]
+                assert pos == qs[u] + (e - qo[u])
+                seen[e] += 1
+        assert np.all(seen == 1)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_chunk_index_random_frontiers(seed):
+    rng = np.random.default_rng(100 + seed)
+    F = int(rng.integers(1, 300))
+    if seed % 3 == 0:
+        degs = rng.integers(1, 40, size=F)
+    elif seed % 3 == 1:
+        degs = np.minimum(rng.zipf(1.5, size=F), 9000)
+    else:
+        degs = rng.integers(1, 20, size=F)
+        degs[rng.integers(0, F)] = 3 * CHUNK + 17   # a hub spanning several chunks
+    check_frontier_chunks(degs.astype(np.int64), rng)
 
 
 def check_frontier(degs, n_warps, rng):
