@@ -140,11 +140,12 @@ coop_status coop_sync(coop_ctx *ctx);
 coop_status coop_get_stats(coop_ctx *ctx, coop_stats *stats);
 
 /*
- * Resize log of the last completed traversal (the runtime's trace): one record per
- * resizing barrier that admitted, removed or launched CTAs, in order, seven int32 each:
- * {barrier index, microseconds since the run started, M_before, k_forked, W_killed,
- * M_after, CTAs launched there by a forced schedule}.  Writes min(cap, available) records
- * to out (host memory, 7*cap int32) and the number written to *n.  At most 4096 records.
+ * Barrier trace of the last completed traversal: one record per resizing barrier (after
+ * the first 2048, only barriers that admitted, removed or launched CTAs), in order,
+ * eight int32 each: {barrier index, microseconds since the run started, M_before,
+ * k_forked, W_killed, M_after, CTAs launched there by a forced schedule, out-edges of the
+ * frontier the next interval expands}.  Writes min(cap, available) records to out (host
+ * memory, 8*cap int32) and the number written to *n.  At most 4096 records per run.
  */
 coop_status coop_get_resize_log(coop_ctx *ctx, int32_t *out, int cap, int *n);
 

@@ -276,15 +276,15 @@ def coop_get_stats(ctx, ok=(COOP_OK,)) -> Stats:
     return s
 
 
-LOG_FIELDS = ("barrier", "t_us", "m_before", "k_forked", "w_killed", "m_after", "spawned")
+LOG_FIELDS = ("barrier", "t_us", "m_before", "k_forked", "w_killed", "m_after", "spawned", "edges")
 
 
 def coop_get_resize_log(ctx, cap: int = 4096):
-    """Resize records of the last traversal: tuples in the order of LOG_FIELDS."""
-    buf = (ctypes.c_int32 * (7 * cap))()
+    """Barrier records of the last traversal: tuples in the order of LOG_FIELDS."""
+    buf = (ctypes.c_int32 * (8 * cap))()
     n = ctypes.c_int(0)
     _check(load_library().coop_get_resize_log(_h(ctx), buf, cap, ctypes.byref(n)), "coop_get_resize_log")
-    return [tuple(buf[7 * i: 7 * i + 7]) for i in range(n.value)]
+    return [tuple(buf[8 * i: 8 * i + 8]) for i in range(n.value)]
 
 
 def coop_set_schedule(ctx, seed: int, p_kill: float, p_fork: float) -> None:

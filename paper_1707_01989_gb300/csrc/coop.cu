@@ -940,7 +940,7 @@ coop_status coop_get_resize_log(coop_ctx *c, int32_t *out, int cap, int *n) {
     LogRec *tmp = new LogRec[take];
     const cudaError_t e = cudaMemcpy(tmp, c->ctl->log, sizeof(LogRec) * (size_t)take, cudaMemcpyDeviceToHost);
     for (int i = 0; e == cudaSuccess && i < take; ++i) {
-      int32_t *r = out + 7 * (size_t)i;
+      int32_t *r = out + 8 * (size_t)i;
       r[0] = tmp[i].barrier;
       r[1] = tmp[i].t_us;
       r[2] = tmp[i].m_before;
@@ -948,6 +948,7 @@ coop_status coop_get_resize_log(coop_ctx *c, int32_t *out, int cap, int *n) {
       r[4] = tmp[i].w;
       r[5] = tmp[i].m_after;
       r[6] = tmp[i].spawned;
+      r[7] = tmp[i].edges;
     }
     delete[] tmp;
     if (cuda_failed(e, "resize log copy")) return COOP_ECUDA;

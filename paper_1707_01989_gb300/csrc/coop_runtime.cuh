@@ -67,11 +67,12 @@ struct Interval {
   uint32_t pad;
 };
 
-// One resize record: barrier index, microseconds since the run started, the active count
-// before, CTAs admitted (fork), CTAs leaving (kill), the active count after, and CTAs
-// launched at this barrier by a forced schedule.
+// One barrier record (the run's trace): barrier index, microseconds since the run
+// started, the active count before, CTAs admitted (fork), CTAs leaving (kill), the active
+// count after, CTAs launched at this barrier by a forced schedule, and the out-edges of
+// the frontier the next interval expands.
 struct LogRec {
-  int32_t barrier, t_us, m_before, k, w, m_after, spawned, pad;
+  int32_t barrier, t_us, m_before, k, w, m_after, spawned, edges;
 };
 
 struct alignas(128) Word {
@@ -393,9 +394,10 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
     c->edges_scanned += edges;
     c->frontier_total += count;
   }
-  if ((k | W | spawned) != 0 && c->log_n < (uint32_t)kLogCap) {
+  // every barrier while the first half of the trace has room, resize events always
+  if (c->log_n < (uint32_t)kLogCap && (c->log_n < (uint32_t)kLogCap / 2u || (k | W | spawned) != 0)) {
     const int32_t t_us = (int32_t)((gtime() - c->t_start) / 1000ull);
-    c->log[c->log_n] = LogRec{c->barriers, t_us, M, k, W, Mn, spawned, 0};
+    c->log[c->log_n] = LogRec{c->barriers, t_us, M, k, W, Mn, spawned, (int32_t)edges};
     c->log_n += 1u;
   }
   nxt.M = Mn;
