@@ -306,7 +306,12 @@ __device__ void expand(const Params &p, const Interval &iv, int32_t id, WarpStag
   while (j < nchunks) {
     // claim the next chunk now; the atomic's latency overlaps this chunk's work
     uint32_t jn = nchunks;
-    if (lane == 0 && GW < nchunks) jn = GW + atomicAdd(&p.ctl->cursor.v, 1u);
+    if (lane == 0 && GW < nchunks) {
+      // offer_kill point: a CTA inside the host's kill target stops claiming chunks (it
+      // finishes the chunk in hand; the others take the rest) and leaves at the barrier
+      if (!(p.coop && doomed(ld_relaxed64(&p.ctl->kill_target), iv.epoch, id)))
+        jn = GW + atomicAdd(&p.ctl->cursor.v, 1u);
+    }
     const uint32_t c0 = j * csize;
     const uint32_t c1 = min(c0 + csize, Etot);
     expand_range<MODE>(p, iv, c0, c1, qx[j * mult], stage, staged, bad, ovf);
@@ -334,19 +339,40 @@ __device__ void spawn_forks(const Params &p, uint32_t n) {
 
 namespace {
 
-// The scheduler warp of the master CTA (the scheduler side of query() and fork):
-// mirrors the host's cumulative kill requests into L2 for the barrier's release path and
-// launches the CTAs the host gives back.  Runs until the traversal is over or the
-// master's own workers have left.
+// The scheduler warp of the master CTA (the scheduler side of query(), kill and fork).
+// It turns the host's outstanding CTA requests into the running interval's kill target
+// (ids >= M - pending leave at their next offer_kill point), publishes how many CTAs
+// have left, and launches the CTAs the host gives back.  Runs until the traversal is
+// over or the master's own workers have left.
 template <int MODE, int NW>
 __device__ __forceinline__ void scheduler_warp(const Params &p, const volatile int32_t *workers_left) {
   Ctl *c = p.ctl;
-  uint32_t kills_seen = p.kill_base, forks_seen = p.fork_base;
+  uint32_t forks_seen = p.fork_base, freed_seen = 0u;
   for (;;) {
     const uint32_t r = ld_sys(&p.mbox->kill_req);
-    if (r != kills_seen) {
-      st_relaxed(&c->kill_req_mirror, r);
-      kills_seen = r;
+    // a consistent (epoch, interval, decided) snapshot: epoch read before and after
+    const uint32_t e = ld_acquire(&c->epoch.v);
+    const uint32_t decided = ld_relaxed(&c->host_decided);
+    const Interval iv = read_iv(c);
+    const int32_t pend = (int32_t)(r - p.kill_base - decided);
+    if (pend > 0 && iv.epoch == e && !iv.done && ld_acquire(&c->epoch.v) == e) {
+      const int32_t T = max(1, iv.M - pend);
+      unsigned long long kt = ld_relaxed64(&c->kill_target);
+      for (;;) {
+        const uint32_t ke = (uint32_t)(kt >> 32);
+        if ((int32_t)(ke - e) > 0) break;  // the word already belongs to a later interval
+        const bool same = ke == e;
+        if (same && ((kt & kTargetClosed) || (int32_t)(kt & 0x7FFFFFFFull) <= T)) break;
+        const unsigned long long nv = ((unsigned long long)e << 32) | (unsigned long long)(uint32_t)T;
+        const unsigned long long prev = atomicCAS(&c->kill_target, kt, nv);
+        if (prev == kt) break;
+        kt = prev;
+      }
+    }
+    const uint32_t sur = ld_relaxed(&c->surrendered);
+    if (sur != freed_seen) {
+      st_sys(&p.mbox->freed, p.kill_base + sur);
+      freed_seen = sur;
     }
     const uint32_t f = ld_sys(&p.mbox->fork_req);
     if ((int32_t)(f - forks_seen) > 0) {
@@ -421,7 +447,6 @@ __global__ void __launch_bounds__(512) coop_init_kernel(const __grid_constant__ 
     if (i < hdr || i >= hdr_end) cw[i] = 0u;
   if (tid == 0) {
     p.ctl->run = p.run;
-    p.ctl->kill_req_mirror = p.kill_base;
     p.ctl->err = 0u;
     p.ctl->done = 0u;
     p.ctl->ovf = 0u;

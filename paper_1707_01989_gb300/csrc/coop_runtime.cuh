@@ -44,7 +44,7 @@ constexpr int kReserveSmem = 116 * 1024;    // dynamic smem of a traversal CTA
 constexpr int kCorunnerSmem = 116 * 1024;   // dynamic smem of a co-runner CTA (sum > SM capacity)
 constexpr uint64_t kEntryGatherNs = 20000;  // master waits this long for its launch to register
 constexpr uint32_t kIndexEdges = 128;       // granularity of the chunk index (edges per unit)
-constexpr uint32_t kChunkUnitsMax = 8;      // a work chunk spans 1..8 units, sized to the frontier
+constexpr uint32_t kChunkUnitsMax = 4;      // a work chunk spans 1..4 units, sized to the frontier
 
 enum Mode : int { MODE_BFS = 0, MODE_SSSP = 1, MODE_BARRIER = 2 };
 
@@ -64,7 +64,7 @@ struct Interval {
   uint32_t edges;  // frontier out-edges (size of this interval's edge space)
   uint32_t done;   // 1: the traversal is over, every CTA leaves
   uint32_t epoch;  // epoch number that opened this interval
-  uint32_t pad;
+  uint32_t doom;   // CTAs of the previous interval with logical id >= doom leave (host kills)
 };
 
 // One barrier record (the run's trace): barrier index, microseconds since the run
@@ -90,9 +90,15 @@ struct Ctl {
   uint64_t pad_q[14];
   alignas(128) Interval iv;  // the current interval (written only by releasers)
   uint32_t pad_iv[24];
+  // host kill target of the running interval: (epoch << 32) | closed << 31 | T, where
+  // CTAs with logical id >= T leave; lowered by the scheduler warp, closed by the releaser
+  alignas(128) unsigned long long kill_target;
+  uint32_t surrendered;   // CTAs that left on a host kill target
+  uint32_t host_decided;  // host kills fixed at closed targets (releaser)
+  uint32_t pad_k[28];
   // header line: written once per run by the init kernel, then by error/done paths
   alignas(128) uint32_t run;
-  uint32_t kill_req_mirror;  // written by the poller warp
+  uint32_t unused_h;
   uint32_t err;              // sticky error (negative coop_status as uint32)
   uint32_t done;             // set by the final release
   uint32_t ovf;              // SSSP distance overflow seen
@@ -101,7 +107,7 @@ struct Ctl {
   uint32_t pad_l[31];
   // releaser-private bookkeeping (serialised by the barrier)
   alignas(128) uint32_t admitted;
-  uint32_t killed_host;
+  uint32_t unused_b;
   int32_t barriers, kills, forks, min_active, max_active, initial_active;
   unsigned long long edges_scanned, frontier_total;
   unsigned long long t_start;  // %globaltimer at the master's entry
@@ -165,6 +171,7 @@ struct CtaShared {
   int32_t ok;
   int32_t exit;
   int32_t workers_left;  // set when this CTA's worker warps have left (bounds the poller)
+  int32_t leave;         // this CTA leaves at the current barrier (host kill)
 };
 
 // ---------------------------------------------------------------- PTX wrappers
@@ -181,6 +188,11 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
 __device__ __forceinline__ uint64_t ld_acquire64(const unsigned long long *p) {
   uint64_t v;
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint64_t ld_relaxed64(const unsigned long long *p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
@@ -246,6 +258,14 @@ __device__ __forceinline__ Interval read_iv(const Ctl *c) {
   return r;
 }
 
+// ---------------------------------------------------------------- host kill target
+constexpr unsigned long long kTargetClosed = 1ull << 31;
+
+// Does the kill target word `kt` make logical id `id` of interval `epoch` leave?
+__device__ __forceinline__ bool doomed(uint64_t kt, uint32_t epoch, int32_t id) {
+  return (uint32_t)(kt >> 32) == epoch && (uint32_t)id >= (uint32_t)(kt & 0x7FFFFFFFull);
+}
+
 // ---------------------------------------------------------------- errors / stats
 __device__ __forceinline__ void raise_err(const Params &p, int code) {
   if (atomicCAS(&p.ctl->err, 0u, (uint32_t)code) == 0u) {
@@ -280,17 +300,21 @@ __device__ __forceinline__ uint64_t slot_pack(uint32_t epoch, uint32_t killed, u
          (uint64_t)(t & 0x7FFFFu);
 }
 
-// Wait until the epoch word differs from `e` (a release happened).  false on error/timeout.
-__device__ __forceinline__ bool wait_release(const Params &p, uint32_t e) {
+// Wait until the epoch word differs from `e` (a release happened): returns 1.  A CTA
+// with logical id `id` (>= 0) that the host's kill target dooms while it waits returns 2
+// at once (it has arrived already, and the closed target will include it).  0 on error
+// or timeout.
+__device__ __forceinline__ int wait_release(const Params &p, uint32_t e, int32_t id = -1) {
   Ctl *c = p.ctl;
   const uint64_t t0 = gtime();
   for (uint32_t spin = 0;; ++spin) {
-    if (ld_acquire(&c->epoch.v) != e) return true;
-    if (ld_relaxed(&c->err) != 0u) return false;
+    if (ld_acquire(&c->epoch.v) != e) return 1;
+    if (id > 0 && doomed(ld_relaxed64(&c->kill_target), e, id)) return 2;
+    if (ld_relaxed(&c->err) != 0u) return 0;
     if ((spin & 31u) == 31u) {
       if (gtime() - t0 > p.timeout_ns) {
         raise_err(p, ERR_TIMEOUT);
-        return false;
+        return 0;
       }
       __nanosleep(spin < 4096 ? 20 : 200);
     }
@@ -345,19 +369,41 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
   nxt.done = (count == 0u || ld_relaxed(&c->err) != 0u) ? 1u : 0u;
 
   const int32_t M = cur.M;
-  int32_t k = 0, W = 0, Wh = 0, spawned = 0;
+  // (5) of the query barrier for the host's requests: close this interval's kill target.
+  // CTAs with ids >= Mmid leave (those that saw the target before arriving already left;
+  // the others leave right after this release).  Targets only decrease, so every CTA that
+  // left early is inside the closed target.
+  int32_t Mmid = M;
+  if (p.coop) {
+    // stamp the word closed for this epoch even when no target was set, so that a
+    // scheduler update computed before this release can no longer land on this epoch
+    unsigned long long kt = ld_relaxed64(&c->kill_target);
+    for (;;) {
+      const uint32_t T = ((uint32_t)(kt >> 32) == cur.epoch) ? (uint32_t)(kt & 0x7FFFFFFFull) : (uint32_t)M;
+      const unsigned long long nv = ((unsigned long long)cur.epoch << 32) | kTargetClosed | (unsigned long long)T;
+      const unsigned long long prev = atomicCAS(&c->kill_target, kt, nv);
+      if (prev == kt) {
+        Mmid = min(M, max(1, (int32_t)T));
+        break;
+      }
+      kt = prev;
+    }
+  }
+  const int32_t Wmid = M - Mmid;
+  c->host_decided += (uint32_t)Wmid;
+  int32_t k = 0, W = 0, spawned = 0;
   uint32_t A = c->admitted;
   if (!nxt.done && p.coop) {
-    // (2) fork: admit CTAs that registered and wait, up to N - M
+    // (2) fork: admit CTAs that registered and wait, up to N - Mmid
     const uint32_t R = ld_relaxed(&c->join_ticket.v);
-    k = (int32_t)min((uint32_t)(p.N - M), R - A);
+    k = (int32_t)min((uint32_t)(p.N - Mmid), R - A);
     int32_t Ws = 0;
     if (p.sched_on) {
       // forced schedule: the scheduler grants up to kcap in [0, N-M] new CTAs (spawned
       // now, admitted when they arrive) and accepts W in [0, M-1] offer_kills
       const uint64_t r = mix64(p.sched_seed ^ mix64((uint64_t)(c->barriers + 1)));
       const uint64_t r2 = mix64(r);
-      const int32_t kcap = ((uint32_t)(r >> 32) < p.p_fork) ? (int32_t)(r2 % (uint64_t)(p.N - M + 1)) : 0;
+      const int32_t kcap = ((uint32_t)(r >> 32) < p.p_fork) ? (int32_t)(r2 % (uint64_t)(p.N - Mmid + 1)) : 0;
       const int32_t pending = (int32_t)(ld_relaxed(&c->launched_total) - 1u - A);
       const int32_t spawn = kcap - pending;
       if (spawn > 0) {
@@ -365,42 +411,39 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
         spawn_forks<MODE, NW>(p, (uint32_t)spawn);
         spawned = spawn;
       }
-      if ((uint32_t)r < p.p_kill) Ws = (int32_t)((r2 >> 32) % (uint64_t)M);
+      if ((uint32_t)r < p.p_kill) Ws = (int32_t)((r2 >> 32) % (uint64_t)Mmid);
     }
-    // (3) query: W = CTAs the scheduler still needs (never CTA 0)
-    const uint32_t req = ld_relaxed(&c->kill_req_mirror);
-    const int32_t pend = (int32_t)(req - p.kill_base - c->killed_host);
-    const int32_t ph = pend > 0 ? pend : 0;
-    W = min(ph + Ws, M + k - 1);
-    Wh = min(ph, W);
+    // (3) query for the forced schedule's kills (never CTA 0)
+    W = min(Ws, Mmid + k - 1);
   }
-  const int32_t Mn = M + k - W;
+  const int32_t Mn = Mmid + k - W;
   for (int32_t i = 0; i < k; ++i) {
     const uint32_t t = A + (uint32_t)i;
-    const uint32_t idv = (uint32_t)(M + i);
+    const uint32_t idv = (uint32_t)(Mmid + i);
     st_relaxed64(&c->slot[t % kMaxCtas], slot_pack(nxt.epoch, idv >= (uint32_t)Mn, idv, t));
   }
   c->admitted = A + (uint32_t)k;
-  if (Wh > 0) {
-    c->killed_host += (uint32_t)Wh;
-    st_sys(&p.mbox->freed, p.kill_base + c->killed_host);
-  }
   c->barriers += 1;
-  c->kills += W;
+  c->kills += Wmid + W;
   c->forks += k;
-  c->min_active = min(c->min_active, Mn);
+  c->min_active = min(c->min_active, min(Mmid, Mn));
   c->max_active = max(c->max_active, Mn);
   if (!nxt.done) {
     c->edges_scanned += edges;
     c->frontier_total += count;
   }
   // every barrier while the first half of the trace has room, resize events always
+  const int32_t t_us = (int32_t)((gtime() - c->t_start) / 1000ull);
+  if (Wmid > 0 && c->log_n < (uint32_t)kLogCap) {  // the host kills of the interval
+    c->log[c->log_n] = LogRec{c->barriers, t_us, M, 0, Wmid, Mmid, 0, (int32_t)edges};
+    c->log_n += 1u;
+  }
   if (c->log_n < (uint32_t)kLogCap && (c->log_n < (uint32_t)kLogCap / 2u || (k | W | spawned) != 0)) {
-    const int32_t t_us = (int32_t)((gtime() - c->t_start) / 1000ull);
-    c->log[c->log_n] = LogRec{c->barriers, t_us, M, k, W, Mn, spawned, (int32_t)edges};
+    c->log[c->log_n] = LogRec{c->barriers, t_us, Mmid, k, W, Mn, spawned, (int32_t)edges};
     c->log_n += 1u;
   }
   nxt.M = Mn;
+  nxt.doom = (uint32_t)Mmid;
   c->iv = nxt;
   if (nxt.done) {
     st_relaxed(&c->done, 1u);
@@ -418,6 +461,9 @@ __device__ __forceinline__ bool resizing_barrier(const Params &p, CtaShared &cs)
   if (threadIdx.x == 0) {
     Ctl *c = p.ctl;
     const Interval cur = cs.iv;
+    // offer_kill: a CTA inside the host's kill target leaves as soon as it arrives (read
+    // before arriving, so the releaser's closed target -- never higher -- includes it)
+    bool leave = p.coop && doomed(ld_relaxed64(&c->kill_target), cur.epoch, cs.id);
     const uint32_t old = atom_add_acq_rel(&c->arrive.v, 1u);
     bool ok = true;
     if (old == (uint32_t)(cur.M - 1) + p.extra_wait) {
@@ -425,14 +471,20 @@ __device__ __forceinline__ bool resizing_barrier(const Params &p, CtaShared &cs)
       st_relaxed(&c->arrive.v, 0u);
       st_release(&c->epoch.v, cur.epoch + 1u);
       cs.iv = nxt;
-    } else {
-      ok = wait_release(p, cur.epoch);
-      if (ok) cs.iv = read_iv(c);
+    } else if (!leave) {
+      const int w = wait_release(p, cur.epoch, p.coop ? cs.id : -1);
+      ok = w != 0;
+      if (w == 1) cs.iv = read_iv(c);
+      if (w == 2) leave = true;
     }
+    // a CTA that waited may still be inside the target as it was closed by the release
+    if (ok && !leave && p.coop && cs.id >= (int32_t)cs.iv.doom) leave = true;  // cs.iv is the new interval here
+    if (leave) atomicAdd(&c->surrendered, 1u);
     cs.ok = ok ? 1 : 0;
+    cs.leave = leave ? 1 : 0;
   }
   workers_sync<NW>();
-  return cs.ok != 0;
+  return cs.ok != 0 && cs.leave == 0;
 }
 
 // ---------------------------------------------------------------- entry
@@ -519,7 +571,7 @@ __device__ __forceinline__ void master_enter(const Params &p, CtaShared &cs) {
   iv.edges = edges;
   iv.done = (count == 0u || ld_relaxed(&c->err) != 0u) ? 1u : 0u;
   iv.epoch = 1u;
-  iv.pad = 0u;
+  iv.doom = (uint32_t)(1 + k);
   c->admitted = (uint32_t)k;
   c->t_start = gtime();
   st_relaxed(&c->launched_total, p.coop ? p.launched : gridDim.x);
