@@ -193,6 +193,57 @@ coop_status coop_sssp_baseline(coop_ctx *ctx, const coop_csr *g, const uint32_t 
 coop_status coop_barrier_bench(coop_ctx *ctx, int32_t n_barriers, int32_t never_arrive,
                                coop_stream stream, coop_stats *stats);
 
+/* ---- batched traversals (many independent jobs in one persistent launch) ---- */
+
+enum { COOP_JOB_BFS = 0, COOP_JOB_SSSP = 1 };
+
+/* One traversal of a batch.  All pointers are caller-owned device memory. */
+typedef struct {
+    coop_csr graph;            /* the job's graph */
+    const uint32_t *d_weights; /* uint32[E] for COOP_JOB_SSSP, ignored for BFS */
+    int32_t source;
+    int32_t kind;              /* COOP_JOB_BFS or COOP_JOB_SSSP */
+    void *d_out;               /* int32 levels[V] (BFS) or uint32 dist[V] (SSSP) */
+} coop_job;
+
+typedef struct coop_batch coop_batch; /* opaque, library-owned */
+
+/*
+ * Prepare a batch of n_jobs independent traversals (the batched form of Sec. 3.2's
+ * traversal: every job is a cooperative kernel of its own -- own barrier, queues and
+ * control block -- and all of them share one persistent launch).  Allocates the jobs'
+ * scratch.  Blocks (CTAs) per job default to one wave of N blocks split in proportion
+ * to the jobs' edges; coop_batch_set_ctas or coop_batch_tune change that.  Batched jobs
+ * have no host scheduler (coop_request_resources / coop_release do not apply).
+ */
+coop_status coop_batch_create(coop_ctx *ctx, const coop_job *jobs, int n_jobs, coop_batch **out);
+
+/* Set the blocks of every job (ctas[i] >= 1; the sum may exceed the resident capacity:
+ * jobs whose blocks are not resident yet start when earlier jobs free their SMs). */
+coop_status coop_batch_set_ctas(coop_batch *b, const int32_t *ctas);
+
+/*
+ * Autotuner: times the batch under candidate apportionments (blocks proportional to
+ * edges^alpha for alpha in {0.5, 0.75, 1}, totals of 1, 2 and 4 waves of N blocks) and
+ * keeps the fastest; ctas_out (nullable, n_jobs entries) receives the choice.
+ * Synchronous; runs the batch 27 times.
+ */
+coop_status coop_batch_tune(coop_batch *b, coop_stream stream, int32_t *ctas_out);
+
+/*
+ * Run every job once: one initialisation kernel and one persistent launch on `stream`.
+ * With use_graph != 0 both are captured once into a CUDA graph (re-captured after the
+ * apportionment changes) and the graph is launched.  Asynchronous.
+ */
+coop_status coop_batch_run(coop_batch *b, coop_stream stream, int use_graph);
+
+/* Per-job statistics of the last run (waits for the device); per_job has n_jobs entries.
+ * Returns the first failing job's status, if any. */
+coop_status coop_batch_get_stats(coop_batch *b, coop_stats *per_job);
+
+/* Free the batch (waits for the device).  NULL is a no-op. */
+coop_status coop_batch_destroy(coop_batch *b);
+
 /*
  * The co-running latency-critical task: y[i] = a * x[i] + y[i] for i < n (fp32,
  * device pointers), on n_ctas CTAs whose shared-memory reservation keeps them off any

@@ -21,7 +21,9 @@ __all__ = [
     "CoopError", "CoopUnavailable", "Stats", "CSR", "coop_init", "coop_destroy", "coop_bfs", "coop_sssp",
     "coop_request_resources", "coop_release", "coop_sync", "coop_get_stats", "coop_get_resize_log",
     "coop_set_schedule", "coop_set_timeout", "coop_set_timing", "coop_query", "coop_bfs_baseline", "coop_sssp_baseline",
-    "coop_barrier_bench", "coop_saxpy", "coop_bfs_noalloc", "coop_status_string", "coop_last_cuda_error", "library_path", "load_library",
+    "coop_barrier_bench", "coop_saxpy", "coop_bfs_noalloc", "coop_status_string", "Job", "Batch", "make_job",
+    "coop_batch_create", "coop_batch_set_ctas", "coop_batch_tune", "coop_batch_run", "coop_batch_get_stats",
+    "coop_batch_destroy", "coop_last_cuda_error", "library_path", "load_library",
 ]
 
 COOP_OK, COOP_EINVAL, COOP_ENOMEM, COOP_ECUDA = 0, -1, -2, -3
@@ -45,6 +47,15 @@ class CSR(ctypes.Structure):
     """coop_csr: V, E and device pointers row_off[V+1], col[E]."""
     _fields_ = [("num_vertices", ctypes.c_int32), ("num_edges", ctypes.c_int64),
                 ("row_off", ctypes.c_void_p), ("col", ctypes.c_void_p)]
+
+
+class Job(ctypes.Structure):
+    """coop_job: one traversal of a batch (device pointers)."""
+    _fields_ = [("graph", CSR), ("d_weights", ctypes.c_void_p), ("source", ctypes.c_int32),
+                ("kind", ctypes.c_int32), ("d_out", ctypes.c_void_p)]
+
+
+COOP_JOB_BFS, COOP_JOB_SSSP = 0, 1
 
 
 class Stats(ctypes.Structure):
@@ -101,6 +112,12 @@ def load_library():
                 "coop_barrier_bench": [vp, i32, i32, vp, sp],
                 "coop_saxpy": [ctypes.c_int, i64, ctypes.c_float, vp, vp, vp],
                 "coop_bfs_noalloc": [cp, i32, vp, vp, vp],
+                "coop_batch_create": [vp, ctypes.POINTER(Job), ctypes.c_int, ctypes.POINTER(vp)],
+                "coop_batch_set_ctas": [vp, ctypes.POINTER(i32)],
+                "coop_batch_tune": [vp, vp, ctypes.POINTER(i32)],
+                "coop_batch_run": [vp, vp, ctypes.c_int],
+                "coop_batch_get_stats": [vp, sp],
+                "coop_batch_destroy": [vp],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -313,6 +330,63 @@ def coop_bfs_noalloc(g: CSR, source: int, levels, status=None, stream=None) -> N
                                          _ptr(levels, "torch.int32", g.num_vertices, "levels"),
                                          _ptr(status, "torch.int32", 1, "status"), _stream(stream))
     _check(st, "coop_bfs_noalloc")
+
+
+class Batch:
+    """Owns a coop_batch pointer and keeps the jobs' tensors alive."""
+
+    def __init__(self, handle: int, n: int, keep):
+        self.handle, self.n, self._keep = handle, n, keep
+
+    def __del__(self):
+        try:
+            coop_batch_destroy(self)
+        except Exception:
+            pass
+
+
+def make_job(g: CSR, source: int, out, weights=None) -> Job:
+    """coop_job for a BFS (weights None) or SSSP traversal writing into `out` ([V] int32 tensor)."""
+    kind = COOP_JOB_BFS if weights is None else COOP_JOB_SSSP
+    return Job(g, _ptr(weights, None, g.num_edges, "weights") if weights is not None else 0, int(source), kind,
+               _ptr(out, None, g.num_vertices, "out"))
+
+
+def coop_batch_create(ctx, jobs, keep=None) -> Batch:
+    arr = (Job * len(jobs))(*jobs)
+    out = ctypes.c_void_p()
+    _check(load_library().coop_batch_create(_h(ctx), arr, len(jobs), ctypes.byref(out)), "coop_batch_create")
+    return Batch(out.value, len(jobs), keep)
+
+
+def coop_batch_set_ctas(batch: Batch, ctas) -> None:
+    arr = (ctypes.c_int32 * batch.n)(*[int(c) for c in ctas])
+    _check(load_library().coop_batch_set_ctas(batch.handle, arr), "coop_batch_set_ctas")
+
+
+def coop_batch_tune(batch: Batch, stream=None):
+    arr = (ctypes.c_int32 * batch.n)()
+    _check(load_library().coop_batch_tune(batch.handle, _stream(stream), arr), "coop_batch_tune")
+    return list(arr)
+
+
+def coop_batch_run(batch: Batch, stream=None, use_graph: bool = True) -> None:
+    _check(load_library().coop_batch_run(batch.handle, _stream(stream), 1 if use_graph else 0), "coop_batch_run")
+
+
+def coop_batch_get_stats(batch: Batch, ok=(COOP_OK,)):
+    arr = (Stats * batch.n)()
+    _check(load_library().coop_batch_get_stats(batch.handle, arr), "coop_batch_get_stats", ok)
+    return list(arr)
+
+
+def coop_batch_destroy(batch) -> None:
+    if isinstance(batch, Batch):
+        if batch.handle:
+            h, batch.handle = batch.handle, 0
+            load_library().coop_batch_destroy(h)
+    elif batch:
+        load_library().coop_batch_destroy(batch)
 
 
 def coop_saxpy(n_ctas: int, a: float, x, y, stream=None) -> None:

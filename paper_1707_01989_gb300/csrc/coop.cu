@@ -26,7 +26,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <numeric>
+#include <vector>
 #include <chrono>
+#include <cmath>
 #include <mutex>
 #include <thread>
 
@@ -398,13 +401,14 @@ __device__ __forceinline__ void worker_loop(const Params &p, CtaShared &cs, Warp
   }
 }
 
+// One CTA's life in a cooperative traversal: enter (as the master, or by registering
+// and waiting to be admitted), then either run the scheduler warp (master only) or the
+// worker loop until the traversal ends or the CTA is killed.
 template <int MODE, int NW>
-__global__ void __launch_bounds__((NW + 1) * 32, 1) coop_traverse(const __grid_constant__ Params p, int join) {
-  __shared__ CtaShared cs;
-  extern __shared__ __align__(16) unsigned char dyn_smem[];  // per-warp enqueue staging (+ SM reservation)
+__device__ __forceinline__ void traverse_body(const Params &p, bool master, CtaShared &cs, unsigned char *dyn) {
   if (threadIdx.x == 0) {
     bool active;
-    if (!join && blockIdx.x == 0) {
+    if (master) {
       master_enter<MODE>(p, cs);
       active = true;
     } else if (p.coop) {
@@ -421,15 +425,47 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) coop_traverse(const __grid_c
     if (p.coop && cs.id == 0 && threadIdx.x == NW * 32) scheduler_warp<MODE, NW>(p, &cs.workers_left);
     return;
   }
-  worker_loop<MODE, NW>(p, cs, reinterpret_cast<WarpStage *>(dyn_smem));
+  worker_loop<MODE, NW>(p, cs, reinterpret_cast<WarpStage *>(dyn));
   if (threadIdx.x == 0) *(volatile int32_t *)&cs.workers_left = 1;
 }
 
-// Per-run initialisation: outputs, scratch and the control block.
+template <int MODE, int NW>
+__global__ void __launch_bounds__((NW + 1) * 32, 1) coop_traverse(const __grid_constant__ Params p, int join) {
+  __shared__ CtaShared cs;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];  // per-warp enqueue staging (+ SM reservation)
+  traverse_body<MODE, NW>(p, !join && blockIdx.x == 0, cs, dyn_smem);
+}
+
+// Many traversals in one persistent launch.  Job g owns blocks [first[g], first[g+1]) and
+// is a cooperative kernel of its own (own control block, queues and barrier); its first
+// block is its master.  A job whose blocks are not resident yet simply starts later:
+// admission is join-on-arrival, so no barrier ever waits for a block that has not run.
+template <int NW>
+__global__ void __launch_bounds__((NW + 1) * 32, 1)
+    coop_traverse_batch(const Params *__restrict__ jobs, const uint32_t *__restrict__ first, int njobs) {
+  __shared__ Params P;
+  __shared__ int32_t s_master;
+  __shared__ CtaShared cs;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = njobs - 1;  // the last job whose first block is <= blockIdx.x
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (first[mid] <= blockIdx.x) lo = mid;
+      else hi = mid - 1;
+    }
+    s_master = first[lo] == blockIdx.x ? 1 : 0;
+    P = jobs[lo];
+  }
+  __syncthreads();
+  if (P.mode == MODE_SSSP) traverse_body<MODE_SSSP, NW>(P, s_master != 0, cs, dyn_smem);
+  else traverse_body<MODE_BFS, NW>(P, s_master != 0, cs, dyn_smem);
+}
+
+// Per-run initialisation: outputs, scratch and the control block (up to its resize log,
+// which is only ever read up to its record count).
 template <int MODE>
-__global__ void __launch_bounds__(512) coop_init_kernel(const __grid_constant__ Params p) {
-  const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const size_t nth = (size_t)gridDim.x * blockDim.x;
+__device__ __forceinline__ void init_body(const Params &p, size_t tid, size_t nth) {
   const size_t V = (size_t)(p.V > 0 ? p.V : 0);
   if (MODE == MODE_BFS) {
     for (size_t i = tid; i < V; i += nth) p.level[i] = -1;
@@ -443,7 +479,7 @@ __global__ void __launch_bounds__(512) coop_init_kernel(const __grid_constant__ 
   // zero the control block except its header line, which thread 0 writes
   uint32_t *cw = reinterpret_cast<uint32_t *>(p.ctl);
   const size_t hdr = offsetof(Ctl, run) / 4, hdr_end = hdr + 32;
-  for (size_t i = tid; i < sizeof(Ctl) / 4; i += nth)
+  for (size_t i = tid; i < offsetof(Ctl, log) / 4; i += nth)
     if (i < hdr || i >= hdr_end) cw[i] = 0u;
   if (tid == 0) {
     p.ctl->run = p.run;
@@ -451,6 +487,22 @@ __global__ void __launch_bounds__(512) coop_init_kernel(const __grid_constant__ 
     p.ctl->done = 0u;
     p.ctl->ovf = 0u;
   }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(512) coop_init_kernel(const __grid_constant__ Params p) {
+  init_body<MODE>(p, (size_t)blockIdx.x * blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x);
+}
+
+// Batch initialisation: blockIdx.y selects the job; its device-resident mailbox is
+// cleared too (batched jobs have no host scheduler).
+__global__ void __launch_bounds__(512) coop_init_batch_kernel(const Params *__restrict__ jobs) {
+  const Params &p = jobs[blockIdx.y];
+  const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (size_t)gridDim.x * blockDim.x;
+  if (p.mode == MODE_SSSP) init_body<MODE_SSSP>(p, tid, nth);
+  else init_body<MODE_BFS>(p, tid, nth);
+  uint32_t *mw = reinterpret_cast<uint32_t *>(p.mbox);
+  for (size_t i = tid; i < sizeof(Mailbox) / 4; i += nth) mw[i] = 0u;
 }
 
 // The co-running task: y = a*x + y, grid-stride, vectorised where aligned.
@@ -673,6 +725,7 @@ coop_status launch_run(coop_ctx *c, const coop_csr *g, const uint32_t *w, int32_
     p.n_barriers = n_barriers;
     p.extra_wait = (uint32_t)std::max(0, extra_wait);
     p.coop = coop ? 1u : 0u;
+    p.mode = MODE;
 
     c->mbox->err = 0;
     c->mbox->status = 0;
@@ -1033,6 +1086,323 @@ coop_status coop_saxpy(int n_ctas, int64_t n, float a, const float *d_x, float *
   });
   coop_saxpy_kernel<<<n_ctas, 1024, kCorunnerSmem, (cudaStream_t)stream>>>(n, a, d_x, d_y);
   return cuda_failed(cudaGetLastError(), "co-runner launch") ? COOP_ECUDA : COOP_OK;
+}
+
+}  // extern "C"
+
+// ===================================================================== batched traversals
+//
+// A batch is a set of independent traversals (jobs) run by one persistent launch of
+// coop_traverse_batch: each job is a cooperative kernel of its own over a contiguous
+// range of blocks.  Jobs are laid out largest first, so that when the grid is larger than
+// what fits on the GPU at once, small jobs fill SMs as big ones finish.  The blocks per
+// job come from coop_batch_set_ctas, the autotuner (coop_batch_tune), or the default
+// rule (proportional to the job's edges, one wave of blocks in total).
+
+struct coop_batch {
+  coop_ctx *ctx = nullptr;
+  int n = 0;
+  std::vector<coop_job> jobs;
+  std::vector<Params> params;   // host copy, in launch order
+  std::vector<int> order;       // launch position -> job index
+  std::vector<int32_t> ctas;    // per job (job order)
+  Params *d_params = nullptr;
+  uint32_t *d_first = nullptr;
+  void *scratch = nullptr;
+  uint32_t total = 0;
+  uint32_t run = 0;
+  cudaGraphExec_t graph = nullptr;
+  bool graph_valid = false;
+  cudaStream_t capture = nullptr;  // private stream the graph is recorded on
+  int64_t max_V = 0;
+};
+
+namespace {
+
+int64_t job_edges(const coop_job &j) { return std::max<int64_t>(j.graph.num_edges, 1); }
+
+// blocks per job proportional to edges^alpha, `total` blocks in all, at least 1 and at
+// most `cap` each (largest-remainder rounding)
+std::vector<int32_t> apportion(const std::vector<coop_job> &jobs, double alpha, int total, int cap) {
+  const int n = (int)jobs.size();
+  std::vector<double> w(n);
+  double sw = 0.0;
+  for (int i = 0; i < n; ++i) sw += (w[i] = std::pow((double)job_edges(jobs[i]), alpha));
+  total = std::max(total, n);
+  std::vector<int32_t> c(n, 1);
+  int left = total - n;
+  std::vector<std::pair<double, int>> rem;
+  for (int i = 0; i < n; ++i) {
+    const double ideal = (double)left * w[i] / sw;
+    const int add = std::min(cap - 1, (int)ideal);
+    c[i] += add;
+    rem.push_back({ideal - add, i});
+  }
+  int used = 0;
+  for (int v : c) used += v;
+  std::sort(rem.begin(), rem.end(), [](auto &a, auto &b) { return a.first > b.first; });
+  for (size_t k = 0; used < total && k < rem.size(); ++k)
+    if (c[rem[k].second] < cap) {
+      ++c[rem[k].second];
+      ++used;
+    }
+  return c;
+}
+
+// (Re)build the device job table for the current block counts.
+coop_status batch_layout(coop_batch *b) {
+  const int n = b->n;
+  b->order.resize(n);
+  std::iota(b->order.begin(), b->order.end(), 0);
+  std::stable_sort(b->order.begin(), b->order.end(),
+                   [&](int x, int y) { return job_edges(b->jobs[x]) > job_edges(b->jobs[y]); });
+  std::vector<uint32_t> first(n);
+  std::vector<Params> ps(n);
+  uint32_t at = 0;
+  for (int k = 0; k < n; ++k) {
+    const int j = b->order[k];
+    first[k] = at;
+    ps[k] = b->params[j];
+    ps[k].launched = (uint32_t)b->ctas[j];
+    ps[k].N = b->ctas[j];
+    at += (uint32_t)b->ctas[j];
+  }
+  b->total = at;
+  if (cuda_failed(cudaMemcpy(b->d_params, ps.data(), sizeof(Params) * n, cudaMemcpyHostToDevice), "batch table") ||
+      cuda_failed(cudaMemcpy(b->d_first, first.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice), "batch table"))
+    return COOP_ECUDA;
+  b->graph_valid = false;
+  return COOP_OK;
+}
+
+void batch_enqueue(coop_batch *b, cudaStream_t s) {
+  coop_ctx *c = b->ctx;
+  const dim3 ig((unsigned)std::max<int64_t>(1, std::min<int64_t>((b->max_V + 511) / 512, 64)), (unsigned)b->n);
+  coop_init_batch_kernel<<<ig, 512, 0, s>>>(b->d_params);
+  switch (c->nw) {
+    case 31: coop_traverse_batch<31><<<b->total, 32 * 32, kReserveSmem, s>>>(b->d_params, b->d_first, b->n); break;
+    case 23: coop_traverse_batch<23><<<b->total, 24 * 32, kReserveSmem, s>>>(b->d_params, b->d_first, b->n); break;
+    default: coop_traverse_batch<15><<<b->total, 16 * 32, kReserveSmem, s>>>(b->d_params, b->d_first, b->n); break;
+  }
+}
+
+const void *batch_fn(int nw) {
+  switch (nw) {
+    case 31: return (const void *)coop_traverse_batch<31>;
+    case 23: return (const void *)coop_traverse_batch<23>;
+    default: return (const void *)coop_traverse_batch<15>;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+coop_status coop_batch_create(coop_ctx *c, const coop_job *jobs, int n, coop_batch **out) {
+  if (!out) return COOP_EINVAL;
+  *out = nullptr;
+  if (!c || !jobs || n < 1 || n > 65535) return COOP_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    const coop_job &j = jobs[i];
+    if (check_graph(&j.graph, j.source) != COOP_OK || !j.d_out) return COOP_EINVAL;
+    if (j.kind != COOP_JOB_BFS && j.kind != COOP_JOB_SSSP) return COOP_EINVAL;
+    if (j.kind == COOP_JOB_SSSP && j.graph.num_edges > 0 && !j.d_weights) return COOP_EINVAL;
+  }
+  DeviceGuard guard(c->device);
+  coop_batch *b = new coop_batch();
+  b->ctx = c;
+  b->n = n;
+  b->jobs.assign(jobs, jobs + n);
+  // scratch per job: control block, mailbox, bitmap or stamps, 2 x 3 queues, 2 chunk indexes
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  std::vector<size_t> off(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    const size_t V = (size_t)jobs[i].graph.num_vertices, X = (size_t)(jobs[i].graph.num_edges / kIndexEdges + 2);
+    const size_t need = al(sizeof(Ctl)) + al(sizeof(Mailbox)) +
+                        (jobs[i].kind == COOP_JOB_SSSP ? al(V * 4) : al((V + 31) / 32 * 4)) + 6 * al(V * 4) +
+                        2 * al(X * 4);
+    off[i + 1] = off[i] + need;
+    b->max_V = std::max<int64_t>(b->max_V, (int64_t)V);
+  }
+  auto fail = [&](coop_status st) {
+    coop_batch_destroy(b);
+    return st;
+  };
+  if (cuda_failed(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking), "capture stream"))
+    return fail(COOP_ECUDA);
+  if (cuda_failed(cudaMalloc(&b->scratch, std::max<size_t>(off[n], 256)), "batch scratch") ||
+      cuda_failed(cudaMalloc((void **)&b->d_params, sizeof(Params) * n), "batch table") ||
+      cuda_failed(cudaMalloc((void **)&b->d_first, sizeof(uint32_t) * n), "batch table"))
+    return fail(COOP_ENOMEM);
+  if (cuda_failed(cudaFuncSetAttribute(batch_fn(c->nw), cudaFuncAttributeMaxDynamicSharedMemorySize, kReserveSmem),
+                  "set batch smem"))
+    return fail(COOP_ECUDA);
+  b->params.resize(n);
+  for (int i = 0; i < n; ++i) {
+    const coop_job &j = jobs[i];
+    char *at = static_cast<char *>(b->scratch) + off[i];
+    auto take = [&](size_t bytes) {
+      char *q = at;
+      at += al(bytes);
+      return q;
+    };
+    const size_t V = (size_t)j.graph.num_vertices, X = (size_t)(j.graph.num_edges / kIndexEdges + 2);
+    Params &p = b->params[i];
+    p = Params{};
+    p.ctl = reinterpret_cast<Ctl *>(take(sizeof(Ctl)));
+    p.mbox = reinterpret_cast<Mailbox *>(take(sizeof(Mailbox)));
+    if (j.kind == COOP_JOB_SSSP) p.stamp = reinterpret_cast<uint32_t *>(take(V * 4));
+    else p.visited = reinterpret_cast<uint32_t *>(take((V + 31) / 32 * 4));
+    for (int q = 0; q < 2; ++q) {
+      p.qv[q] = reinterpret_cast<uint32_t *>(take(V * 4));
+      p.qs[q] = reinterpret_cast<uint32_t *>(take(V * 4));
+      p.qo[q] = reinterpret_cast<uint32_t *>(take(V * 4));
+    }
+    for (int q = 0; q < 2; ++q) p.qx[q] = reinterpret_cast<uint32_t *>(take(X * 4));
+    p.row_off = j.graph.row_off;
+    p.col = j.graph.col;
+    p.V = j.graph.num_vertices;
+    p.E = (uint32_t)j.graph.num_edges;
+    p.src = j.source;
+    p.mode = j.kind == COOP_JOB_SSSP ? MODE_SSSP : MODE_BFS;
+    if (j.kind == COOP_JOB_SSSP) {
+      p.w = j.d_weights;
+      p.dist = static_cast<uint32_t *>(j.d_out);
+    } else {
+      p.level = static_cast<int32_t *>(j.d_out);
+    }
+    p.timeout_ns = (uint64_t)std::max<int64_t>(c->timeout_us, 1) * 1000ull;
+    p.run = 1u;
+    p.coop = 1u;
+  }
+  b->ctas = apportion(b->jobs, 1.0, c->N, c->N);
+  const coop_status st = batch_layout(b);
+  if (st != COOP_OK) return fail(st);
+  *out = b;
+  return COOP_OK;
+}
+
+coop_status coop_batch_set_ctas(coop_batch *b, const int32_t *ctas) {
+  if (!b || !ctas) return COOP_EINVAL;
+  for (int i = 0; i < b->n; ++i)
+    if (ctas[i] < 1 || ctas[i] > kMaxCtas) return COOP_EINVAL;
+  DeviceGuard guard(b->ctx->device);
+  b->ctas.assign(ctas, ctas + b->n);
+  return batch_layout(b);
+}
+
+coop_status coop_batch_run(coop_batch *b, coop_stream stream, int use_graph) {
+  if (!b) return COOP_EINVAL;
+  DeviceGuard guard(b->ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!use_graph) {
+    batch_enqueue(b, s);
+    return cuda_failed(cudaGetLastError(), "batch launch") ? COOP_ECUDA : COOP_OK;
+  }
+  if (!b->graph_valid) {
+    if (b->graph) {
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+    }
+    // recorded on a private stream (the caller's may be the legacy default stream, which
+    // cannot be captured), then launched on the caller's stream
+    cudaGraph_t g = nullptr;
+    if (cuda_failed(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal), "begin capture"))
+      return COOP_ECUDA;
+    batch_enqueue(b, b->capture);
+    const cudaError_t e = cudaStreamEndCapture(b->capture, &g);
+    if (cuda_failed(e, "end capture")) return COOP_ECUDA;
+    const cudaError_t ie = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (cuda_failed(ie, "graph instantiate")) return COOP_ECUDA;
+    b->graph_valid = true;
+  }
+  return cuda_failed(cudaGraphLaunch(b->graph, s), "graph launch") ? COOP_ECUDA : COOP_OK;
+}
+
+coop_status coop_batch_tune(coop_batch *b, coop_stream stream, int32_t *ctas_out) {
+  if (!b) return COOP_EINVAL;
+  coop_ctx *c = b->ctx;
+  DeviceGuard guard(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cuda_failed(cudaEventCreate(&e0), "event") || cuda_failed(cudaEventCreate(&e1), "event")) return COOP_ECUDA;
+  // candidate rules: blocks proportional to edges^alpha, `waves` x N blocks in total
+  const double alphas[] = {0.5, 0.75, 1.0};
+  const int waves[] = {1, 2, 4};
+  float best = 1e30f;
+  std::vector<int32_t> best_ctas = b->ctas;
+  coop_status st = COOP_OK;
+  for (double a : alphas)
+    for (int wv : waves) {
+      b->ctas = apportion(b->jobs, a, wv * c->N, c->N);
+      if ((st = batch_layout(b)) != COOP_OK) break;
+      float ms = 0.f, tot = 0.f;
+      for (int rep = 0; rep < 3; ++rep) {
+        cudaEventRecord(e0, s);
+        batch_enqueue(b, s);
+        cudaEventRecord(e1, s);
+        if (cuda_failed(cudaEventSynchronize(e1), "tune run")) {
+          st = COOP_ECUDA;
+          break;
+        }
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) tot += ms;  // first run warms up
+      }
+      if (st != COOP_OK) break;
+      if (tot < best) {
+        best = tot;
+        best_ctas = b->ctas;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != COOP_OK) return st;
+  b->ctas = best_ctas;
+  st = batch_layout(b);
+  if (ctas_out) std::copy(b->ctas.begin(), b->ctas.end(), ctas_out);
+  return st;
+}
+
+coop_status coop_batch_get_stats(coop_batch *b, coop_stats *per_job) {
+  if (!b || !per_job) return COOP_EINVAL;
+  DeviceGuard guard(b->ctx->device);
+  if (cuda_failed(cudaDeviceSynchronize(), "batch sync")) return COOP_ECUDA;
+  coop_status worst = COOP_OK;
+  for (int i = 0; i < b->n; ++i) {
+    Mailbox m;
+    if (cuda_failed(cudaMemcpy(&m, b->params[i].mbox, sizeof(Mailbox), cudaMemcpyDeviceToHost), "batch stats"))
+      return COOP_ECUDA;
+    coop_stats &st = per_job[i];
+    memset(&st, 0, sizeof(st));
+    st.levels = m.levels;
+    st.barriers = m.barriers;
+    st.kills = m.kills;
+    st.forks = m.forks;
+    st.min_active = m.min_active;
+    st.max_active = m.max_active;
+    st.initial_active = m.initial_active;
+    st.ctas_launched = m.ctas_launched;
+    st.edges_scanned = (int64_t)m.edges_scanned;
+    st.frontier_total = (int64_t)m.frontier_total;
+    st.status = m.err != 0 ? m.err : (m.run_done == b->params[i].run ? m.status : (int32_t)COOP_ETIMEOUT);
+    if (st.status != COOP_OK && worst == COOP_OK) worst = (coop_status)st.status;
+  }
+  return worst;
+}
+
+coop_status coop_batch_destroy(coop_batch *b) {
+  if (!b) return COOP_OK;
+  DeviceGuard guard(b->ctx->device);
+  cudaDeviceSynchronize();
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->capture) cudaStreamDestroy(b->capture);
+  if (b->scratch) cudaFree(b->scratch);
+  if (b->d_params) cudaFree(b->d_params);
+  if (b->d_first) cudaFree(b->d_first);
+  (void)cudaGetLastError();
+  delete b;
+  return COOP_OK;
 }
 
 }  // extern "C"

@@ -163,6 +163,7 @@ struct Params {
   int32_t n_barriers;  // MODE_BARRIER: intervals to run
   uint32_t extra_wait; // barrier self-test: arrivals that never come
   uint32_t coop;       // 0: non-cooperative baseline (fixed ids, no scheduler)
+  int32_t mode;        // MODE_BFS / MODE_SSSP (read by the batch kernel)
 };
 
 struct CtaShared {
