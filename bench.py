@@ -468,6 +468,86 @@ def corunner(coop, ctx, dev, csr, src, lv, stream, period_s=1.0 / 60.0, duration
             "coop_slowdown": round(per_co / per_alone, 4)}
 
 
+def batched(coop, ctx, dev, stream, flush, n_inst=64, seed=3, steps=5):
+    """Batched form: 64 independent R-MAT instances (scales uniform in 12..20, edge factor
+    16), a BFS and an SSSP job each, run as one autotuned, CUDA-graph-captured launch,
+    against one launch per job (the same 128 traversals issued back to back)."""
+    import numpy as np
+    import torch
+    import graphgen as gg
+    import oracle
+    rng = np.random.default_rng(seed)
+    scales = rng.integers(12, 21, size=n_inst)
+    keep, jobs, outs = [], [], []
+    es_total, edges_total = 0, 0
+    singles = []
+    for i, sc in enumerate(scales):
+        g = gg.rmat(int(sc), 16, seed=1000 + i)
+        w = gg.weights(g, 2000 + i)
+        src = gg.max_out_degree_vertex(g)
+        ro = torch.from_numpy(np.array(g.row_off)).to(dev)
+        col = torch.from_numpy(np.array(g.col)).to(dev)
+        wt = torch.from_numpy(w.view(np.int32)).to(dev)
+        lv = torch.empty(g.num_vertices, dtype=torch.int32, device=dev)
+        dist = torch.empty(g.num_vertices, dtype=torch.int32, device=dev)
+        csr = coop.make_csr(ro, col)
+        keep += [ro, col, wt, lv, dist, csr]
+        jobs += [coop.make_job(csr, src, lv), coop.make_job(csr, src, dist, wt)]
+        outs.append((g, w, src, lv, dist))
+        singles.append((csr, src, lv, wt, dist))
+        edges_total += g.num_edges
+    b = coop.coop_batch_create(ctx, jobs, keep)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    ctas = coop.coop_batch_tune(b, stream)
+    tune_s = time.perf_counter() - t0
+
+    def timed(fn, reps):
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    run = lambda: coop.coop_batch_run(b, stream, use_graph=True)
+    run()
+    ms_batch = timed(run, steps)
+    stats = coop.coop_batch_get_stats(b)
+
+    def one_per_job():
+        for csr, src, lv, wt, dist in singles:
+            coop.coop_bfs(ctx, csr, src, lv, stream=stream)
+            coop.coop_sssp(ctx, csr, wt, src, dist, stream=stream)
+
+    one_per_job()
+    ms_single = timed(one_per_job, max(2, steps // 2))
+    # parity of the batched results (run once more, then compare every job)
+    run()
+    torch.cuda.synchronize(dev)
+    exact = 0
+    for g, w, src, lv, dist in outs:
+        l = lv.cpu().numpy()
+        d = dist.cpu().numpy().view(np.uint32)
+        exact += int(np.array_equal(l, oracle.bfs(g, src))) + int(np.array_equal(d, oracle.dijkstra(g, w, src)))
+        deg = np.diff(g.row_off.astype(np.int64))
+        es_total += int(deg[l >= 0].sum()) * 2  # BFS and SSSP reach the same vertices
+    return {"instances": int(n_inst), "jobs": len(jobs), "scales": [int(x) for x in scales],
+            "edges_total": int(edges_total), "E_s_total": int(es_total),
+            "batch_ms": round(ms_batch, 3), "one_launch_per_job_ms": round(ms_single, 3),
+            "gteps_batched": round(es_total / (ms_batch / 1e3) / 1e9, 3),
+            "gteps_one_per_job": round(es_total / (ms_single / 1e3) / 1e9, 3),
+            "speedup": round(ms_single / ms_batch, 3), "graph_captured": True,
+            "tuned_ctas_total": int(sum(ctas)), "tune_s": round(tune_s, 2),
+            "jobs_bit_exact": exact, "all_ok": all(s.status == 0 for s in stats)}
+
+
 def secondary(coop, ctx, dev, stream, flush, args):
     """BFS on R-MAT 22, grid BFS, barrier latency and the non-cooperative baseline ratio."""
     import numpy as np
@@ -529,6 +609,7 @@ def secondary(coop, ctx, dev, stream, flush, args):
     ok = bool(np.array_equal(lv.cpu().numpy(), np.add(*np.divmod(np.arange(65536), 256))))
     out["grid_bfs"] = {"levels": 511, "ms": round(ms, 4), "kernel_us": round(kus, 2),
                        "us_per_level": round(kus / 511, 3), "closed_form_ok": ok}
+    out["batched"] = batched(coop, ctx, dev, stream, flush)
     # empty resizing barriers at M = N
     n = 20000
     f = lambda: coop.coop_barrier_bench(ctx, n, stream=stream, stats=False)
