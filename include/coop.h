@@ -35,6 +35,7 @@
 #ifndef COOP_H
 #define COOP_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -77,6 +78,8 @@ typedef struct {
     int32_t reserved;
     int64_t edges_scanned;  /* sum of out-degrees over every frontier (BFS: E_s) */
     int64_t frontier_total; /* sum of frontier sizes */
+    int64_t vertices_reached; /* V_r: vertices reached from the source (incl. it) */
+    int64_t reached_edges;  /* E_s: out-edges of the reached vertices (the TEPS numerator) */
     double gather_us_max;   /* longest coop_request_resources wait during the run */
     double kernel_us;       /* persistent-kernel time on the launch stream (0 unless timing is on) */
 } coop_stats;
@@ -243,6 +246,57 @@ coop_status coop_batch_get_stats(coop_batch *b, coop_stats *per_job);
 
 /* Free the batch (waits for the device).  NULL is a no-op. */
 coop_status coop_batch_destroy(coop_batch *b);
+
+/* ---- serving: a request loop with continuous batching ---- */
+
+typedef struct coop_server coop_server; /* opaque, library-owned */
+
+/* The outcome of one query. */
+typedef struct {
+    int32_t status;    /* coop_status of the traversal */
+    int32_t slot;      /* slot that ran it */
+    int32_t ctas;      /* CTAs it was admitted with */
+    int32_t reserved;
+    double queue_us;   /* submit -> launch */
+    double latency_us; /* submit -> completion seen by the server */
+    coop_stats stats;  /* the traversal's statistics */
+} coop_query_result;
+
+/*
+ * Create a server on `device` with `slots` concurrent query slots (each a context of its
+ * own).  hbm_budget_bytes (0 = no limit) bounds the scratch the slots may hold for the
+ * registered graphs; coop_server_add_graph fails with COOP_ENOMEM beyond it.
+ */
+coop_status coop_server_create(int device, int slots, size_t hbm_budget_bytes, coop_server **out);
+
+/*
+ * Register a device-resident graph (caller-owned CSR and optional weights, which must
+ * stay valid until the server is destroyed) before the first query.  Sizes every
+ * slot's scratch for it.  *graph_id receives its index.
+ */
+coop_status coop_server_add_graph(coop_server *sv, const coop_csr *g, const uint32_t *d_weights, int *graph_id);
+
+/*
+ * Queue a query: kind COOP_JOB_BFS (d_out int32[V]) or COOP_JOB_SSSP (d_out uint32[V],
+ * the graph must have weights) from `source` on graph `graph_id`.  Queries are admitted
+ * in arrival order as slots free up; a query that arrives while others run overlaps with
+ * them: running traversals are shrunk (offer_kill) so that every running query holds an
+ * equal share of the CTAs, and grown back (request_fork) when queries finish.  Never
+ * blocks.  *ticket identifies the query.
+ */
+coop_status coop_server_submit(coop_server *sv, int graph_id, int kind, int32_t source, void *d_out,
+                               uint64_t *ticket);
+
+/* Wait for a query (timeout_us <= 0: no limit) and fetch its result; returns its status. */
+coop_status coop_server_wait(coop_server *sv, uint64_t ticket, int timeout_us, coop_query_result *res);
+
+/* Take n_ctas CTAs from the running queries for a co-running task (blocking, like
+ * coop_request_resources), and give them back. */
+coop_status coop_server_request_resources(coop_server *sv, int n_ctas, int timeout_us, int *n_freed);
+coop_status coop_server_release(coop_server *sv, int n_ctas);
+
+/* Drain the queue, wait for running queries and free everything.  NULL is a no-op. */
+coop_status coop_server_destroy(coop_server *sv);
 
 /*
  * The co-running latency-critical task: y[i] = a * x[i] + y[i] for i < n (fp32,

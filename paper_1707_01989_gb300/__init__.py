@@ -23,7 +23,9 @@ __all__ = [
     "coop_set_schedule", "coop_set_timeout", "coop_set_timing", "coop_query", "coop_bfs_baseline", "coop_sssp_baseline",
     "coop_barrier_bench", "coop_saxpy", "coop_bfs_noalloc", "coop_status_string", "Job", "Batch", "make_job",
     "coop_batch_create", "coop_batch_set_ctas", "coop_batch_tune", "coop_batch_run", "coop_batch_get_stats",
-    "coop_batch_destroy", "coop_last_cuda_error", "library_path", "load_library",
+    "coop_batch_destroy", "coop_last_cuda_error", "library_path", "load_library", "Server", "QueryResult",
+    "coop_server_create", "coop_server_add_graph", "coop_server_submit", "coop_server_wait",
+    "coop_server_request_resources", "coop_server_release", "coop_server_destroy",
 ]
 
 COOP_OK, COOP_EINVAL, COOP_ENOMEM, COOP_ECUDA = 0, -1, -2, -3
@@ -65,10 +67,18 @@ class Stats(ctypes.Structure):
                 ("initial_active", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("ctas_launched", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("edges_scanned", ctypes.c_int64), ("frontier_total", ctypes.c_int64),
+                ("vertices_reached", ctypes.c_int64), ("reached_edges", ctypes.c_int64),
                 ("gather_us_max", ctypes.c_double), ("kernel_us", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class QueryResult(ctypes.Structure):
+    """coop_query_result: one served query's outcome."""
+    _fields_ = [("status", ctypes.c_int32), ("slot", ctypes.c_int32), ("ctas", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("queue_us", ctypes.c_double), ("latency_us", ctypes.c_double),
+                ("stats", Stats)]
 
 
 _lib = None
@@ -118,6 +128,13 @@ def load_library():
                 "coop_batch_run": [vp, vp, ctypes.c_int],
                 "coop_batch_get_stats": [vp, sp],
                 "coop_batch_destroy": [vp],
+                "coop_server_create": [ctypes.c_int, ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(vp)],
+                "coop_server_add_graph": [vp, cp, vp, ip],
+                "coop_server_submit": [vp, ctypes.c_int, ctypes.c_int, i32, vp, ctypes.POINTER(u64)],
+                "coop_server_wait": [vp, u64, ctypes.c_int, ctypes.POINTER(QueryResult)],
+                "coop_server_request_resources": [vp, ctypes.c_int, ctypes.c_int, ip],
+                "coop_server_release": [vp, ctypes.c_int],
+                "coop_server_destroy": [vp],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -387,6 +404,69 @@ def coop_batch_destroy(batch) -> None:
             load_library().coop_batch_destroy(h)
     elif batch:
         load_library().coop_batch_destroy(batch)
+
+
+class Server:
+    """Owns a coop_server pointer and the registered graphs' tensors."""
+
+    def __init__(self, handle: int):
+        self.handle, self._keep = handle, []
+
+    def __del__(self):
+        try:
+            coop_server_destroy(self)
+        except Exception:
+            pass
+
+
+def coop_server_create(device: int = 0, slots: int = 4, hbm_budget_bytes: int = 0) -> Server:
+    out = ctypes.c_void_p()
+    _check(load_library().coop_server_create(int(device), int(slots), int(hbm_budget_bytes), ctypes.byref(out)),
+           "coop_server_create")
+    return Server(out.value)
+
+
+def coop_server_add_graph(sv: Server, g: CSR, weights=None, keep=()) -> int:
+    gid = ctypes.c_int(-1)
+    _check(load_library().coop_server_add_graph(sv.handle, ctypes.byref(g),
+                                                _ptr(weights, None, g.num_edges, "weights") if weights is not None
+                                                else None, ctypes.byref(gid)), "coop_server_add_graph")
+    sv._keep.append((g, weights, keep))
+    return gid.value
+
+
+def coop_server_submit(sv: Server, graph_id: int, kind: int, source: int, out) -> int:
+    t = ctypes.c_uint64(0)
+    _check(load_library().coop_server_submit(sv.handle, int(graph_id), int(kind), int(source),
+                                             _ptr(out, None, None, "out"), ctypes.byref(t)), "coop_server_submit")
+    return t.value
+
+
+def coop_server_wait(sv: Server, ticket: int, timeout_us: int = 0, ok=(COOP_OK,)) -> QueryResult:
+    r = QueryResult()
+    _check(load_library().coop_server_wait(sv.handle, ctypes.c_uint64(ticket), int(timeout_us), ctypes.byref(r)),
+           "coop_server_wait", ok)
+    return r
+
+
+def coop_server_request_resources(sv: Server, n_ctas: int, timeout_us: int = 0, ok=(COOP_OK,)) -> int:
+    n = ctypes.c_int(0)
+    _check(load_library().coop_server_request_resources(sv.handle, int(n_ctas), int(timeout_us), ctypes.byref(n)),
+           "coop_server_request_resources", ok)
+    return n.value
+
+
+def coop_server_release(sv: Server, n_ctas: int) -> None:
+    _check(load_library().coop_server_release(sv.handle, int(n_ctas)), "coop_server_release")
+
+
+def coop_server_destroy(sv) -> None:
+    if isinstance(sv, Server):
+        if sv.handle:
+            h, sv.handle = sv.handle, 0
+            load_library().coop_server_destroy(h)
+    elif sv:
+        load_library().coop_server_destroy(sv)
 
 
 def coop_saxpy(n_ctas: int, a: float, x, y, stream=None) -> None:

@@ -26,6 +26,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <condition_variable>
+#include <deque>
+#include <unordered_map>
 #include <numeric>
 #include <vector>
 #include <chrono>
@@ -164,7 +168,7 @@ constexpr int kUnroll = 4;  // 32-edge chunks a warp has in flight per iteration
 template <int MODE>
 __device__ __forceinline__ void expand_range(const Params &p, const Interval &iv, uint32_t c0, uint32_t c1,
                                              uint32_t wb, WarpStage &stage, uint32_t &staged, bool &bad,
-                                             bool &ovf) {
+                                             bool &ovf, uint32_t &nreach, uint64_t &ereach) {
   const unsigned lane = threadIdx.x & 31u;
   const uint32_t Etot = iv.edges;
   const uint32_t F = iv.count;
@@ -243,6 +247,8 @@ __device__ __forceinline__ void expand_range(const Params &p, const Interval &iv
           p.level[vv[u]] = (int32_t)next_level;
           if (row_of(p, vv[u], rs, deg)) push = deg > 0u;
           else bad = true;
+          nreach += 1u;
+          ereach += deg;
         }
         stage_push<MODE>(p, out, stage, staged, push, vv[u], rs, deg, lane);
       }
@@ -268,13 +274,21 @@ __device__ __forceinline__ void expand_range(const Params &p, const Interval &iv
             ovf = true;
           } else {
             const uint32_t nd = (uint32_t)nd64;
-            if (nd < dv[u] && nd < atomicMin(p.dist + vv[u], nd)) {
+            uint32_t old = 0u;
+            if (nd < dv[u] && nd < (old = atomicMin(p.dist + vv[u], nd))) {
               const uint32_t tag = next_level + 1u;  // stamp of "queued for the next round"
               uint32_t *sv = p.stamp + vv[u];
               if (*(volatile uint32_t *)sv != tag && atomicExch(sv, tag) != tag) {
                 if (row_of(p, vv[u], rs, deg)) push = deg > 0u;
                 else bad = true;
+              } else if (old == 0xFFFFFFFFu) {
+                row_of(p, vv[u], rs, deg);
               }
+              if (old == 0xFFFFFFFFu) {  // first time this vertex is reached
+                nreach += 1u;
+                ereach += deg;
+              }
+              if (!push) deg = 0u;
             }
           }
         }
@@ -304,7 +318,8 @@ __device__ void expand(const Params &p, const Interval &iv, int32_t id, WarpStag
   if (j >= nchunks) return;
   const uint32_t *qx = iv.sel ? p.qx[1] : p.qx[0];
   const uint32_t out = iv.sel ^ 1u;
-  uint32_t staged = 0u;
+  uint32_t staged = 0u, nreach = 0u;
+  uint64_t ereach = 0ull;
   bool bad = false, ovf = false;
   while (j < nchunks) {
     // claim the next chunk now; the atomic's latency overlaps this chunk's work
@@ -317,10 +332,19 @@ __device__ void expand(const Params &p, const Interval &iv, int32_t id, WarpStag
     }
     const uint32_t c0 = j * csize;
     const uint32_t c1 = min(c0 + csize, Etot);
-    expand_range<MODE>(p, iv, c0, c1, qx[j * mult], stage, staged, bad, ovf);
+    expand_range<MODE>(p, iv, c0, c1, qx[j * mult], stage, staged, bad, ovf, nreach, ereach);
     j = __shfl_sync(kFull, jn, 0);
   }
   if (staged) stage_flush<MODE>(p, out, stage, staged, lane);
+  // this warp's newly reached vertices and their out-edges (the TEPS numerator)
+  for (int o = 16; o > 0; o >>= 1) {
+    nreach += __shfl_xor_sync(kFull, nreach, o);
+    ereach += __shfl_xor_sync(kFull, ereach, o);
+  }
+  if (lane == 0 && nreach) {
+    atomicAdd(&p.ctl->reached, (unsigned long long)nreach);
+    atomicAdd(&p.ctl->reached_edges, (unsigned long long)ereach);
+  }
   if (bad) raise_err(p, ERR_GRAPH);
   if (ovf) p.ctl->ovf = 1u;
 }
@@ -994,6 +1018,8 @@ coop_status coop_get_stats(coop_ctx *c, coop_stats *s) {
   s->ctas_launched = m->ctas_launched;
   s->edges_scanned = (int64_t)m->edges_scanned;
   s->frontier_total = (int64_t)m->frontier_total;
+  s->vertices_reached = (int64_t)m->reached;
+  s->reached_edges = (int64_t)m->reached_edges;
   s->gather_us_max = c->gather_us_max;
   if (c->timing && c->launched) {
     float ms = 0.f;
@@ -1385,6 +1411,8 @@ coop_status coop_batch_get_stats(coop_batch *b, coop_stats *per_job) {
     st.ctas_launched = m.ctas_launched;
     st.edges_scanned = (int64_t)m.edges_scanned;
     st.frontier_total = (int64_t)m.frontier_total;
+    st.vertices_reached = (int64_t)m.reached;
+    st.reached_edges = (int64_t)m.reached_edges;
     st.status = m.err != 0 ? m.err : (m.run_done == b->params[i].run ? m.status : (int32_t)COOP_ETIMEOUT);
     if (st.status != COOP_OK && worst == COOP_OK) worst = (coop_status)st.status;
   }
@@ -1402,6 +1430,333 @@ coop_status coop_batch_destroy(coop_batch *b) {
   if (b->d_first) cudaFree(b->d_first);
   (void)cudaGetLastError();
   delete b;
+  return COOP_OK;
+}
+
+}  // extern "C"
+
+// ===================================================================== serving loop
+//
+// A request loop with continuous batching.  Queries (BFS or SSSP from a source on one of
+// the registered, device-resident graphs) are admitted in arrival order whenever a slot is
+// free and the HBM budget allows; each admitted query runs as its own cooperative
+// traversal in its slot (a context of its own, its own stream).  Queries that arrive
+// while others run overlap with them: the dispatcher shrinks the running traversals
+// (coop_request_resources, i.e. offer_kill at their next chunk boundary) so that every
+// running query holds an equal share of the CTAs, and when a query finishes its CTAs are
+// returned to the survivors (coop_release, i.e. request_fork).  A co-runner can take CTAs
+// from the whole server the same way.
+
+struct coop_server {
+  int device = 0;
+  int N = 0;           // CTAs of the GPU (one per SM)
+  int min_share = 1;   // a running query never drops below this many CTAs
+  size_t budget = 0, per_slot = 0;
+  struct Slot {
+    coop_ctx *ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    int64_t req = -1;  // running request, -1 when idle
+    int share = 0;     // CTAs the dispatcher means this query to hold
+  };
+  std::vector<Slot> slots;
+  struct Graph {
+    coop_csr g;
+    const uint32_t *w;
+  };
+  std::vector<Graph> graphs;
+  struct Req {
+    int graph, kind;
+    int32_t src;
+    void *out;
+    double t_submit = 0, t_start = 0, t_done = 0;
+    int status = 1;  // 1 = pending / running
+    int slot = -1, ctas = 0;
+    coop_stats st{};
+  };
+  std::unordered_map<uint64_t, Req> reqs;
+  std::deque<uint64_t> queue;
+  uint64_t next_ticket = 1;
+  int corunner_held = 0;  // CTAs lent to a co-runner
+  std::mutex mu;
+  std::condition_variable cv;
+  std::thread worker;
+  bool stop = false, started = false;
+};
+
+namespace {
+
+double now_us() {
+  return std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+int running_count(const coop_server *sv) {
+  int n = 0;
+  for (const auto &sl : sv->slots) n += sl.req >= 0;
+  return n;
+}
+
+// Give every running query an equal share of the CTAs not held by a co-runner: take CTAs
+// from queries above the share (they leave at their next offer_kill point) and return CTAs
+// to queries below it (forked into them).
+void rebalance_locked(coop_server *sv) {
+  const int run = running_count(sv);
+  if (run == 0) return;
+  const int avail = std::max(run * sv->min_share, sv->N - sv->corunner_held);
+  const int share = std::max(sv->min_share, avail / run);
+  for (auto &sl : sv->slots) {
+    if (sl.req < 0) continue;
+    if (sl.share > share) {
+      int freed = 0;
+      coop_request_resources(sl.ctx, sl.share - share, 1, &freed);  // posts the request; does not wait
+      sl.share = share;
+    } else if (sl.share < share) {
+      int lent = 0;
+      coop_query(sl.ctx, nullptr, nullptr, nullptr, &lent);
+      const int give = std::min(share - sl.share, lent);
+      if (give > 0 && coop_release(sl.ctx, give) == COOP_OK) sl.share += give;
+    }
+  }
+}
+
+void dispatcher(coop_server *sv) {
+  DeviceGuard guard(sv->device);
+  std::unique_lock<std::mutex> lk(sv->mu);
+  for (;;) {
+    bool changed = false;
+    // completions
+    for (size_t i = 0; i < sv->slots.size(); ++i) {
+      auto &sl = sv->slots[i];
+      if (sl.req < 0 || cudaEventQuery(sl.done) != cudaSuccess) continue;
+      auto &r = sv->reqs[(uint64_t)sl.req];
+      r.t_done = now_us();
+      const coop_status st = coop_get_stats(sl.ctx, &r.st);
+      r.status = (int)st;
+      sl.req = -1;
+      sl.share = 0;
+      changed = true;
+    }
+    // admissions, in arrival order
+    while (!sv->queue.empty()) {
+      int free_slot = -1;
+      for (size_t i = 0; i < sv->slots.size(); ++i)
+        if (sv->slots[i].req < 0) {
+          free_slot = (int)i;
+          break;
+        }
+      if (free_slot < 0) break;
+      const uint64_t t = sv->queue.front();
+      sv->queue.pop_front();
+      auto &r = sv->reqs[t];
+      auto &sl = sv->slots[(size_t)free_slot];
+      const int run = running_count(sv) + 1;
+      const int avail = std::max(run * sv->min_share, sv->N - sv->corunner_held);
+      const int share = std::max(sv->min_share, avail / run);
+      // the new query starts with `share` CTAs: lend the rest of its slot's CTAs away
+      int lent = 0;
+      coop_query(sl.ctx, nullptr, nullptr, nullptr, &lent);
+      const int want_lent = sv->N - share;
+      if (lent < want_lent) coop_request_resources(sl.ctx, want_lent - lent, 0, nullptr);  // idle: immediate
+      else if (lent > want_lent) coop_release(sl.ctx, lent - want_lent);
+      sl.req = (int64_t)t;
+      sl.share = share;
+      r.slot = free_slot;
+      r.ctas = share;
+      r.t_start = now_us();
+      const auto &G = sv->graphs[(size_t)r.graph];
+      coop_status st = r.kind == COOP_JOB_SSSP
+                           ? coop_sssp(sl.ctx, &G.g, G.w, r.src, static_cast<uint32_t *>(r.out), sl.stream, nullptr)
+                           : coop_bfs(sl.ctx, &G.g, r.src, static_cast<int32_t *>(r.out), sl.stream, nullptr);
+      if (st == COOP_OK) st = cuda_failed(cudaEventRecord(sl.done, sl.stream), "query event") ? COOP_ECUDA : COOP_OK;
+      if (st != COOP_OK) {
+        r.status = (int)st;
+        r.t_done = now_us();
+        sl.req = -1;
+      }
+      changed = true;
+    }
+    if (changed) {
+      rebalance_locked(sv);
+      sv->cv.notify_all();
+    }
+    if (sv->stop && sv->queue.empty() && running_count(sv) == 0) break;
+    if (!changed) sv->cv.wait_for(lk, std::chrono::microseconds(running_count(sv) ? 5 : 200));
+  }
+  sv->cv.notify_all();
+}
+
+}  // namespace
+
+extern "C" {
+
+coop_status coop_server_create(int device, int slots, size_t hbm_budget_bytes, coop_server **out) {
+  if (!out) return COOP_EINVAL;
+  *out = nullptr;
+  if (slots < 1 || slots > 64) return COOP_EINVAL;
+  coop_server *sv = new coop_server();
+  sv->device = device;
+  sv->budget = hbm_budget_bytes;
+  for (int i = 0; i < slots; ++i) {
+    coop_server::Slot sl;
+    coop_status st = coop_init(device, 0, 0, &sl.ctx);
+    if (st != COOP_OK) {
+      coop_server_destroy(sv);
+      return st;
+    }
+    DeviceGuard guard(device);
+    if (cuda_failed(cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking), "slot stream") ||
+        cuda_failed(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming), "slot event")) {
+      sv->slots.push_back(sl);
+      coop_server_destroy(sv);
+      return COOP_ECUDA;
+    }
+    sv->slots.push_back(sl);
+  }
+  coop_query(sv->slots[0].ctx, &sv->N, nullptr, nullptr, nullptr);
+  *out = sv;
+  return COOP_OK;
+}
+
+coop_status coop_server_add_graph(coop_server *sv, const coop_csr *g, const uint32_t *d_weights, int *graph_id) {
+  if (!sv || !graph_id || check_graph(g, 0) != COOP_OK) return COOP_EINVAL;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  if (sv->started) return COOP_EBUSY;  // graphs are registered before the first query
+  // every slot must be able to serve the graph: size its scratch now, before serving,
+  // since an allocation while queries run would wait for them
+  const size_t per = (size_t)g->num_vertices * 4 * 8 + (size_t)(g->num_edges / kIndexEdges + 2) * 8 + (1u << 20);
+  const size_t per_slot = std::max(sv->per_slot, per);
+  if (sv->budget && per_slot * sv->slots.size() > sv->budget) return COOP_ENOMEM;
+  for (auto &sl : sv->slots) {
+    DeviceGuard guard(sv->device);
+    std::lock_guard<std::mutex> lk2(sl.ctx->mu);
+    const coop_status st = ensure_scratch(sl.ctx, g->num_vertices, g->num_edges);
+    if (st != COOP_OK) return st;
+  }
+  sv->per_slot = per_slot;
+  sv->graphs.push_back({*g, d_weights});
+  *graph_id = (int)sv->graphs.size() - 1;
+  return COOP_OK;
+}
+
+coop_status coop_server_submit(coop_server *sv, int graph_id, int kind, int32_t source, void *d_out,
+                               uint64_t *ticket) {
+  if (!sv || !ticket || !d_out || (kind != COOP_JOB_BFS && kind != COOP_JOB_SSSP)) return COOP_EINVAL;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  if (graph_id < 0 || graph_id >= (int)sv->graphs.size()) return COOP_EINVAL;
+  const auto &G = sv->graphs[(size_t)graph_id];
+  if (source < 0 || source >= G.g.num_vertices) return COOP_EINVAL;
+  if (kind == COOP_JOB_SSSP && G.g.num_edges > 0 && !G.w) return COOP_EINVAL;
+  if (!sv->started) {
+    sv->started = true;
+    sv->worker = std::thread(dispatcher, sv);
+  }
+  coop_server::Req r;
+  r.graph = graph_id;
+  r.kind = kind;
+  r.src = source;
+  r.out = d_out;
+  r.t_submit = now_us();
+  const uint64_t t = sv->next_ticket++;
+  sv->reqs[t] = r;
+  sv->queue.push_back(t);
+  *ticket = t;
+  sv->cv.notify_all();
+  return COOP_OK;
+}
+
+coop_status coop_server_wait(coop_server *sv, uint64_t ticket, int timeout_us, coop_query_result *res) {
+  if (!sv) return COOP_EINVAL;
+  std::unique_lock<std::mutex> lk(sv->mu);
+  auto it = sv->reqs.find(ticket);
+  if (it == sv->reqs.end()) return COOP_EINVAL;
+  auto done = [&] { return it->second.status != 1; };
+  if (timeout_us > 0) {
+    if (!sv->cv.wait_for(lk, std::chrono::microseconds(timeout_us), done)) return COOP_ETIMEOUT;
+  } else {
+    sv->cv.wait(lk, done);
+  }
+  const auto &r = it->second;
+  if (res) {
+    res->status = r.status;
+    res->slot = r.slot;
+    res->ctas = r.ctas;
+    res->queue_us = r.t_start - r.t_submit;
+    res->latency_us = r.t_done - r.t_submit;
+    res->stats = r.st;
+  }
+  const int st = r.status;
+  sv->reqs.erase(it);
+  return (coop_status)st;
+}
+
+coop_status coop_server_request_resources(coop_server *sv, int n_ctas, int timeout_us, int *n_freed) {
+  if (n_freed) *n_freed = 0;
+  if (!sv || n_ctas < 1) return COOP_EINVAL;
+  std::vector<std::pair<coop_ctx *, int>> asks;
+  int from_idle = 0;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->corunner_held + n_ctas > sv->N - sv->min_share) return COOP_EINVAL;
+    // CTAs that neither a running query nor the co-runner holds are free already
+    int held = sv->corunner_held;
+    std::vector<size_t> idx;
+    for (size_t i = 0; i < sv->slots.size(); ++i)
+      if (sv->slots[i].req >= 0) {
+        idx.push_back(i);
+        held += sv->slots[i].share;
+      }
+    from_idle = std::min(n_ctas, std::max(0, sv->N - held));
+    int need = n_ctas - from_idle;
+    // the rest from the running queries, largest share first
+    std::sort(idx.begin(), idx.end(), [&](size_t x, size_t y) { return sv->slots[x].share > sv->slots[y].share; });
+    for (size_t i : idx) {
+      if (need <= 0) break;
+      auto &sl = sv->slots[i];
+      const int take = std::min(need, sl.share - sv->min_share);
+      if (take <= 0) continue;
+      sl.share -= take;
+      need -= take;
+      asks.push_back({sl.ctx, take});
+    }
+    sv->corunner_held += n_ctas;
+  }
+  int got = from_idle;
+  coop_status worst = COOP_OK;
+  for (auto &a : asks) {
+    int f = 0;
+    const coop_status st = coop_request_resources(a.first, a.second, timeout_us, &f);
+    got += f;
+    if (st != COOP_OK) worst = st;
+  }
+  if (n_freed) *n_freed = got;
+  return worst;
+}
+
+coop_status coop_server_release(coop_server *sv, int n_ctas) {
+  if (!sv || n_ctas < 1) return COOP_EINVAL;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  if (n_ctas > sv->corunner_held) return COOP_EINVAL;
+  sv->corunner_held -= n_ctas;
+  rebalance_locked(sv);
+  return COOP_OK;
+}
+
+coop_status coop_server_destroy(coop_server *sv) {
+  if (!sv) return COOP_OK;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stop = true;
+    sv->cv.notify_all();
+  }
+  if (sv->worker.joinable()) sv->worker.join();
+  DeviceGuard guard(sv->device);
+  for (auto &sl : sv->slots) {
+    if (sl.ctx) coop_destroy(sl.ctx);
+    if (sl.done) cudaEventDestroy(sl.done);
+    if (sl.stream) cudaStreamDestroy(sl.stream);
+  }
+  (void)cudaGetLastError();
+  delete sv;
   return COOP_OK;
 }
 

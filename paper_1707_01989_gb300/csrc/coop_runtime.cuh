@@ -105,6 +105,9 @@ struct Ctl {
   uint32_t pad_h[27];
   alignas(128) uint32_t launched_total;  // CTAs launched for this run (main grid + forks)
   uint32_t pad_l[31];
+  alignas(128) unsigned long long reached_edges;  // out-edges of reached vertices (E_s)
+  unsigned long long reached;                     // reached vertices (V_r)
+  uint64_t pad_r[14];
   // releaser-private bookkeeping (serialised by the barrier)
   alignas(128) uint32_t admitted;
   uint32_t unused_b;
@@ -129,6 +132,7 @@ struct alignas(128) Mailbox {
   int32_t levels, barriers, kills, forks, min_active, max_active, initial_active, status;
   int32_t ctas_launched, pad2;
   unsigned long long edges_scanned, frontier_total;
+  unsigned long long reached, reached_edges;
 };
 
 // Kernel parameters: immutable for the whole run and identical for forked CTAs
@@ -288,6 +292,8 @@ __device__ __forceinline__ void publish_stats(const Params &p, int status) {
   st_sys((uint32_t *)&m->status, (uint32_t)status);
   st_sys((uint32_t *)&m->ctas_launched, ld_relaxed(&c->launched_total));
   st_sys64(&m->edges_scanned, c->edges_scanned);
+  st_sys64(&m->reached, ld_relaxed64(&c->reached));
+  st_sys64(&m->reached_edges, ld_relaxed64(&c->reached_edges));
   st_sys64(&m->frontier_total, c->frontier_total);
   __threadfence_system();
   st_sys(&m->run_done, p.run);
@@ -543,6 +549,8 @@ __device__ __forceinline__ void master_enter(const Params &p, CtaShared &cs) {
         p.dist[s] = 0u;
         p.stamp[s] = 1u;
       }
+      c->reached = 1ull;
+      c->reached_edges = (unsigned long long)(re - rs);
       if (re > rs) {
         p.qo[0][0] = 0u;
         p.qs[0][0] = (uint32_t)rs;

@@ -49,6 +49,7 @@ def test_bfs_rmat_matches_oracle(ctx, scale, ef, seed):
     assert_same(lv, exp, f"rmat{scale} levels")
     vr, es = oracle.traversal_work(g, exp >= 0)
     assert st.edges_scanned == es
+    assert (st.vertices_reached, st.reached_edges) == (vr, es)
     # a level is expanded when some vertex on it has out-edges
     assert st.levels == exp[(exp >= 0) & (g.out_degree() > 0)].max() + 1
 
@@ -59,7 +60,9 @@ def test_sssp_rmat_matches_oracle(ctx, scale, ef, seed):
     w = gg.weights(g, seed + 1)
     src = gg.max_out_degree_vertex(g)
     d, st = run_sssp(ctx, DevGraph(g, w), src)
-    assert_same(d, oracle.dijkstra(g, w, src), f"rmat{scale} dist")
+    exp = oracle.dijkstra(g, w, src)
+    assert_same(d, exp, f"rmat{scale} dist")
+    assert (st.vertices_reached, st.reached_edges) == oracle.traversal_work(g, exp != oracle.UNREACHED_DIST)
 
 
 def test_random_graphs_many_sources(ctx):
