@@ -548,6 +548,125 @@ def batched(coop, ctx, dev, stream, flush, n_inst=64, seed=3, steps=5):
             "jobs_bit_exact": exact, "all_ok": all(s.status == 0 for s in stats)}
 
 
+def serving(coop, dev, n_graphs=32, rate=200.0, duration_s=3.0, slots=4, budget=60 << 30):
+    """Serving: a Poisson stream of BFS / SSSP queries (50/50, random sources) on 32
+    device-resident R-MAT graphs of scales 14..21, admitted by the server under a 60 GB
+    HBM budget, with the periodic saxpy co-runner taking half the SMs every 16.7 ms.
+    Also the saturation throughput (every query submitted at once) with `slots` slots
+    against one query at a time (a single slot: one launch per query)."""
+    import numpy as np
+    import torch
+    import graphgen as gg
+    import oracle
+    rng_g, rng_a, rng_s = (np.random.default_rng(x) for x in (4, 5, 6))
+    scales = rng_g.integers(14, 22, size=n_graphs)
+    graphs = []
+    for i, sc in enumerate(scales):
+        g = gg.rmat(int(sc), 16, seed=3000 + i)
+        w = gg.weights(g, 4000 + i)
+        ro = torch.from_numpy(np.array(g.row_off)).to(dev)
+        col = torch.from_numpy(np.array(g.col)).to(dev)
+        wt = torch.from_numpy(w.view(np.int32)).to(dev)
+        graphs.append((g, w, ro, col, wt, coop.make_csr(ro, col)))
+    maxV = max(x[0].num_vertices for x in graphs)
+    n_q = int(rate * duration_s)
+    gaps = rng_a.exponential(1.0 / rate, size=n_q)
+    qs = []
+    for i in range(n_q):
+        gi = int(rng_s.integers(0, n_graphs))
+        qs.append((gi, coop.COOP_JOB_BFS if rng_s.random() < 0.5 else coop.COOP_JOB_SSSP,
+                   int(rng_s.integers(0, graphs[gi][0].num_vertices))))
+    outs = [torch.empty(maxV, dtype=torch.int32, device=dev) for _ in range(64)]
+
+    def make_server(k):
+        sv = coop.coop_server_create(dev.index or 0, slots=k, hbm_budget_bytes=budget)
+        for g, w, ro, col, wt, csr in graphs:
+            coop.coop_server_add_graph(sv, csr, wt)
+        return sv
+
+    # open loop: Poisson arrivals with the co-runner alongside
+    sv = make_server(slots)
+    N = coop.coop_query(coop.coop_init(dev.index or 0))["max_ctas"]
+    x = torch.rand(16 * 1024 * 1024, device=dev)
+    y = torch.rand(16 * 1024 * 1024, device=dev)
+    cs = torch.cuda.Stream(device=dev, priority=-1)
+    for _ in range(3):
+        coop.coop_saxpy(N // 2, 2.0, x, y, stream=cs)
+    cs.synchronize()
+    lat_co, stop = [], threading.Event()
+
+    def ticker():
+        nxt = time.perf_counter()
+        while not stop.is_set():
+            t0 = time.perf_counter()
+            coop.coop_server_request_resources(sv, N // 2, timeout_us=2000,
+                                               ok=(coop.COOP_OK, coop.COOP_ETIMEOUT))
+            coop.coop_saxpy(N // 2, 2.0, x, y, stream=cs)
+            cs.synchronize()
+            coop.coop_server_release(sv, N // 2)
+            lat_co.append((time.perf_counter() - t0) * 1e3)
+            nxt += 1.0 / 60.0
+            time.sleep(max(0.0, nxt - time.perf_counter()))
+
+    import collections
+    pending, done = collections.deque(), []
+    th = threading.Thread(target=ticker)
+    th.start()
+    t_start = time.perf_counter()
+    due = t_start
+    for i, (gi, kind, src) in enumerate(qs):
+        due += gaps[i]
+        time.sleep(max(0.0, due - time.perf_counter()))
+        if len(pending) >= 48:  # output buffers are reused: at most 48 queries outstanding
+            done.append(coop.coop_server_wait(sv, pending.popleft()[1]))
+        pending.append((i, coop.coop_server_submit(sv, gi, kind, src, outs[i % 64])))
+    while pending:
+        done.append(coop.coop_server_wait(sv, pending.popleft()[1]))
+    wall = time.perf_counter() - t_start
+    stop.set()
+    th.join()
+    coop.coop_server_destroy(sv)
+    lat = sorted(r.latency_us / 1e3 for r in done)
+    es = sum(r.stats.reached_edges for r in done)
+    # results of the mix equal the oracle (the last 8 queries, whose outputs are intact)
+    exact = 0
+    for i in range(max(0, n_q - 8), n_q):
+        gi, kind, src = qs[i]
+        g, w = graphs[gi][0], graphs[gi][1]
+        got = outs[i % 64][: g.num_vertices].cpu().numpy()
+        exp = oracle.bfs(g, src) if kind == coop.COOP_JOB_BFS else oracle.dijkstra(g, w, src).view(np.int32)
+        exact += int(np.array_equal(got, exp))
+
+    def pct(v, q):
+        v = sorted(v)
+        return round(v[min(len(v) - 1, int(round(q * (len(v) - 1))))], 4)
+
+    # saturation: all queries at once, `slots` slots vs one slot
+    def saturate(k):
+        sv2 = make_server(k)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        ts = [coop.coop_server_submit(sv2, gi, kind, src, outs[i]) for i, (gi, kind, src) in enumerate(qs[:64])]
+        rs = [coop.coop_server_wait(sv2, t) for t in ts]
+        dt = time.perf_counter() - t0
+        coop.coop_server_destroy(sv2)
+        return sum(r.stats.reached_edges for r in rs) / dt / 1e9, dt * 1e3
+
+    g_multi, ms_multi = saturate(slots)
+    g_one, ms_one = saturate(1)
+    return {"graphs": n_graphs, "scales": [int(x) for x in scales], "queries": len(done), "rate_per_s": rate,
+            "slots": slots, "hbm_budget_gb": budget >> 30, "wall_s": round(wall, 3),
+            "latency_ms_p50": pct(lat, 0.5), "latency_ms_p99": pct(lat, 0.99),
+            "gteps_open_loop": round(es / wall / 1e9, 3),
+            "saturation_gteps": round(g_multi, 3), "saturation_ms": round(ms_multi, 2),
+            "saturation_gteps_one_at_a_time": round(g_one, 3), "saturation_ms_one_at_a_time": round(ms_one, 2),
+            "served_vs_one_at_a_time": round(g_multi / g_one, 3),
+            "corunner_jobs": len(lat_co), "corunner_ms_p50": pct(lat_co, 0.5) if lat_co else None,
+            "corunner_ms_p99": pct(lat_co, 0.99) if lat_co else None,
+            "last_queries_bit_exact": f"{exact}/8",
+            "all_ok": all(r.status == 0 for r in done)}
+
+
 def secondary(coop, ctx, dev, stream, flush, args):
     """BFS on R-MAT 22, grid BFS, barrier latency and the non-cooperative baseline ratio."""
     import numpy as np
@@ -610,6 +729,7 @@ def secondary(coop, ctx, dev, stream, flush, args):
     out["grid_bfs"] = {"levels": 511, "ms": round(ms, 4), "kernel_us": round(kus, 2),
                        "us_per_level": round(kus / 511, 3), "closed_form_ok": ok}
     out["batched"] = batched(coop, ctx, dev, stream, flush)
+    out["serving"] = serving(coop, dev)
     # empty resizing barriers at M = N
     n = 20000
     f = lambda: coop.coop_barrier_bench(ctx, n, stream=stream, stats=False)

@@ -290,9 +290,15 @@ coop_status coop_server_submit(coop_server *sv, int graph_id, int kind, int32_t 
 /* Wait for a query (timeout_us <= 0: no limit) and fetch its result; returns its status. */
 coop_status coop_server_wait(coop_server *sv, uint64_t ticket, int timeout_us, coop_query_result *res);
 
-/* Take n_ctas CTAs from the running queries for a co-running task (blocking, like
- * coop_request_resources), and give them back. */
+/*
+ * Take n_ctas CTAs for a co-running task: CTAs no running query holds count first, the
+ * rest is requested from the running queries, largest share first (each keeps at least
+ * one).  Blocks like coop_request_resources, at most timeout_us per query; returns
+ * COOP_ETIMEOUT with *n_freed < n_ctas if fewer could be freed in time (the requests stay
+ * pending).  The n_ctas are held for the co-runner either way until coop_server_release.
+ */
 coop_status coop_server_request_resources(coop_server *sv, int n_ctas, int timeout_us, int *n_freed);
+/* Give n_ctas co-runner CTAs back; running queries grow into them (request_fork). */
 coop_status coop_server_release(coop_server *sv, int n_ctas);
 
 /* Drain the queue, wait for running queries and free everything.  NULL is a no-op. */

@@ -1490,6 +1490,12 @@ double now_us() {
   return std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// CTAs a slot's context can still lend: CTA 0 is never surrendered.
+int lendable(coop_ctx *c) {
+  std::lock_guard<std::mutex> lk(c->mu);
+  return std::max(0, c->N - 1 - (int)(c->kill_req - c->returned));
+}
+
 int running_count(const coop_server *sv) {
   int n = 0;
   for (const auto &sl : sv->slots) n += sl.req >= 0;
@@ -1507,9 +1513,10 @@ void rebalance_locked(coop_server *sv) {
   for (auto &sl : sv->slots) {
     if (sl.req < 0) continue;
     if (sl.share > share) {
+      const int take = std::min(sl.share - share, lendable(sl.ctx));
       int freed = 0;
-      coop_request_resources(sl.ctx, sl.share - share, 1, &freed);  // posts the request; does not wait
-      sl.share = share;
+      if (take > 0) coop_request_resources(sl.ctx, take, 1, &freed);  // posts the request; does not wait
+      sl.share -= take;
     } else if (sl.share < share) {
       int lent = 0;
       coop_query(sl.ctx, nullptr, nullptr, nullptr, &lent);
@@ -1712,7 +1719,7 @@ coop_status coop_server_request_resources(coop_server *sv, int n_ctas, int timeo
     for (size_t i : idx) {
       if (need <= 0) break;
       auto &sl = sv->slots[i];
-      const int take = std::min(need, sl.share - sv->min_share);
+      const int take = std::min(std::min(need, sl.share - sv->min_share), lendable(sl.ctx));
       if (take <= 0) continue;
       sl.share -= take;
       need -= take;
@@ -1726,9 +1733,10 @@ coop_status coop_server_request_resources(coop_server *sv, int n_ctas, int timeo
     int f = 0;
     const coop_status st = coop_request_resources(a.first, a.second, timeout_us, &f);
     got += f;
-    if (st != COOP_OK) worst = st;
+    if (st != COOP_OK && worst == COOP_OK) worst = st;
   }
   if (n_freed) *n_freed = got;
+  if (worst == COOP_OK && got < n_ctas) worst = COOP_ETIMEOUT;  // fewer CTAs could be taken
   return worst;
 }
 
