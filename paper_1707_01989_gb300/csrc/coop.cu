@@ -183,6 +183,25 @@ __device__ __forceinline__ void expand_range(const Params &p, const Interval &iv
 
   Window w;
   load_entry<MODE>(p, qo, qs, qv, F, Etot, wb + lane, w);
+  // the index names the entry holding the 128-edge unit boundary at or before c0; slide
+  // (32 entries at most per step) until lane 0 holds the entry containing c0
+  for (;;) {
+    const unsigned ended = __ballot_sync(kFull, w.end <= c0);
+    if (!ended) break;
+    const unsigned n = (unsigned)__popc(ended);
+    wb += n;
+    const unsigned srcl = (lane + n) & 31u;
+    Window s;
+    s.off = __shfl_sync(kFull, w.off, srcl);
+    s.end = __shfl_sync(kFull, w.end, srcl);
+    s.start = __shfl_sync(kFull, w.start, srcl);
+    if (MODE == MODE_SSSP) {
+      s.u = __shfl_sync(kFull, w.u, srcl);
+      s.du = __shfl_sync(kFull, w.du, srcl);
+    }
+    if (lane + n < 32u) w = s;
+    else load_entry<MODE>(p, qo, qs, qv, F, Etot, wb + lane, w);
+  }
 
   for (uint32_t c = c0; c < E1; c += 32u * kUnroll) {
     uint32_t pos[kUnroll], du[kUnroll];
@@ -299,8 +318,8 @@ __device__ __forceinline__ void expand_range(const Params &p, const Interval &iv
 }
 
 // Expand this warp's part of the interval.  The edge space is cut into chunks of
-// kIndexEdges * mult edges, mult in [1, kChunkUnitsMax] chosen so that small frontiers
-// still spread over every warp.  A warp's first chunk is fixed by its logical position
+// 32 * mult edges, mult in [1, kChunkUnitsMax] chosen so that small frontiers still
+// spread over every warp.  A warp's first chunk is fixed by its logical position
 // -- chunk id*NW + warp, Fig. 4's tid/stride split recomputed from the current M -- and
 // further chunks are claimed from one counter, so warps that drew cheap chunks take
 // over the rest.  The enqueue built a chunk index (entry holding each unit's first
@@ -310,9 +329,9 @@ __device__ void expand(const Params &p, const Interval &iv, int32_t id, WarpStag
   const unsigned lane = threadIdx.x & 31u;
   const uint32_t Etot = iv.edges;
   const uint32_t GW = (uint32_t)iv.M * NW;
-  const uint32_t units = (Etot + kIndexEdges - 1u) / kIndexEdges;
+  const uint32_t units = (Etot + 31u) / 32u;
   const uint32_t mult = max(1u, min(kChunkUnitsMax, (units + GW - 1u) / GW));
-  const uint32_t csize = kIndexEdges * mult;
+  const uint32_t csize = 32u * mult;
   const uint32_t nchunks = (units + mult - 1u) / mult;
   uint32_t j = (uint32_t)id * NW + (threadIdx.x >> 5);
   if (j >= nchunks) return;
@@ -332,7 +351,7 @@ __device__ void expand(const Params &p, const Interval &iv, int32_t id, WarpStag
     }
     const uint32_t c0 = j * csize;
     const uint32_t c1 = min(c0 + csize, Etot);
-    expand_range<MODE>(p, iv, c0, c1, qx[j * mult], stage, staged, bad, ovf, nreach, ereach);
+    expand_range<MODE>(p, iv, c0, c1, qx[c0 / kIndexEdges], stage, staged, bad, ovf, nreach, ereach);
     j = __shfl_sync(kFull, jn, 0);
   }
   if (staged) stage_flush<MODE>(p, out, stage, staged, lane);

@@ -44,7 +44,7 @@ constexpr int kReserveSmem = 116 * 1024;    // dynamic smem of a traversal CTA
 constexpr int kCorunnerSmem = 116 * 1024;   // dynamic smem of a co-runner CTA (sum > SM capacity)
 constexpr uint64_t kEntryGatherNs = 20000;  // master waits this long for its launch to register
 constexpr uint32_t kIndexEdges = 128;       // granularity of the chunk index (edges per unit)
-constexpr uint32_t kChunkUnitsMax = 4;      // a work chunk spans 1..4 units, sized to the frontier
+constexpr uint32_t kChunkUnitsMax = 16;     // a work chunk spans 1..16 32-edge units, sized to the frontier
 
 enum Mode : int { MODE_BFS = 0, MODE_SSSP = 1, MODE_BARRIER = 2 };
 
@@ -355,6 +355,33 @@ __device__ void spawn_forks(const Params &p, uint32_t n);
 template <int MODE, int NW>
 __device__ __forceinline__ Interval release_step(const Params &p, const Interval cur) {
   Ctl *c = p.ctl;
+  // Everything the release needs is loaded first, in one batch of independent loads:
+  // the output queue's counters and the releaser-private books.
+  const uint32_t out = cur.sel ^ 1u;
+  const unsigned long long packed = (MODE == MODE_BARRIER) ? 0ull : c->qctr[out];
+  const uint32_t A = c->admitted;
+  const uint32_t decided = c->host_decided;
+  const int32_t barriers = c->barriers + 1, kills0 = c->kills, forks0 = c->forks;
+  const int32_t mina = c->min_active, maxa = c->max_active;
+  const unsigned long long es0 = c->edges_scanned, ft0 = c->frontier_total, t_start = c->t_start;
+  uint32_t log_n = c->log_n;
+  const uint32_t err = ld_relaxed(&c->err);
+  const uint32_t R = p.coop ? ld_relaxed(&c->join_ticket.v) : 0u;
+  const int32_t M = cur.M;
+  // (5) of the query barrier for the host's requests: close this interval's kill target.
+  // CTAs with ids >= Mmid leave (those that saw it while waiting already left; the
+  // others leave right after this release).  The word is stamped closed for this epoch
+  // even when no target was set, so that a scheduler update computed before this
+  // release can no longer land on this epoch; a lower open target is then put back.
+  int32_t Mmid = M;
+  unsigned long long closed = 0ull;
+  if (p.coop) {
+    closed = ((unsigned long long)cur.epoch << 32) | kTargetClosed;
+    const unsigned long long kt = atomicExch(&c->kill_target, closed | (unsigned long long)(uint32_t)M);
+    if ((uint32_t)(kt >> 32) == cur.epoch) Mmid = min(M, max(1, (int32_t)(kt & 0x7FFFFFFFull)));
+  }
+  if (Mmid < M) st_relaxed64(&c->kill_target, closed | (unsigned long long)(uint32_t)Mmid);
+
   Interval nxt = cur;
   nxt.epoch = cur.epoch + 1u;
   nxt.level = cur.level + 1;
@@ -363,8 +390,6 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
     count = (cur.level + 1 < p.n_barriers) ? 1u : 0u;
     edges = 0u;
   } else {
-    const uint32_t out = cur.sel ^ 1u;
-    const unsigned long long packed = c->qctr[out];
     count = (uint32_t)(packed >> 32);
     edges = (uint32_t)packed;
     c->qctr[cur.sel] = 0ull;  // the finished input queue becomes the next output queue
@@ -373,42 +398,18 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
   }
   nxt.count = count;
   nxt.edges = edges;
-  nxt.done = (count == 0u || ld_relaxed(&c->err) != 0u) ? 1u : 0u;
+  nxt.done = (count == 0u || err != 0u) ? 1u : 0u;
 
-  const int32_t M = cur.M;
-  // (5) of the query barrier for the host's requests: close this interval's kill target.
-  // CTAs with ids >= Mmid leave (those that saw the target before arriving already left;
-  // the others leave right after this release).  Targets only decrease, so every CTA that
-  // left early is inside the closed target.
-  int32_t Mmid = M;
-  if (p.coop) {
-    // stamp the word closed for this epoch even when no target was set, so that a
-    // scheduler update computed before this release can no longer land on this epoch
-    unsigned long long kt = ld_relaxed64(&c->kill_target);
-    for (;;) {
-      const uint32_t T = ((uint32_t)(kt >> 32) == cur.epoch) ? (uint32_t)(kt & 0x7FFFFFFFull) : (uint32_t)M;
-      const unsigned long long nv = ((unsigned long long)cur.epoch << 32) | kTargetClosed | (unsigned long long)T;
-      const unsigned long long prev = atomicCAS(&c->kill_target, kt, nv);
-      if (prev == kt) {
-        Mmid = min(M, max(1, (int32_t)T));
-        break;
-      }
-      kt = prev;
-    }
-  }
   const int32_t Wmid = M - Mmid;
-  c->host_decided += (uint32_t)Wmid;
   int32_t k = 0, W = 0, spawned = 0;
-  uint32_t A = c->admitted;
   if (!nxt.done && p.coop) {
     // (2) fork: admit CTAs that registered and wait, up to N - Mmid
-    const uint32_t R = ld_relaxed(&c->join_ticket.v);
     k = (int32_t)min((uint32_t)(p.N - Mmid), R - A);
     int32_t Ws = 0;
     if (p.sched_on) {
       // forced schedule: the scheduler grants up to kcap in [0, N-M] new CTAs (spawned
       // now, admitted when they arrive) and accepts W in [0, M-1] offer_kills
-      const uint64_t r = mix64(p.sched_seed ^ mix64((uint64_t)(c->barriers + 1)));
+      const uint64_t r = mix64(p.sched_seed ^ mix64((uint64_t)barriers));
       const uint64_t r2 = mix64(r);
       const int32_t kcap = ((uint32_t)(r >> 32) < p.p_fork) ? (int32_t)(r2 % (uint64_t)(p.N - Mmid + 1)) : 0;
       const int32_t pending = (int32_t)(ld_relaxed(&c->launched_total) - 1u - A);
@@ -430,32 +431,33 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
     st_relaxed64(&c->slot[t % kMaxCtas], slot_pack(nxt.epoch, idv >= (uint32_t)Mn, idv, t));
   }
   c->admitted = A + (uint32_t)k;
-  c->barriers += 1;
-  c->kills += Wmid + W;
-  c->forks += k;
-  c->min_active = min(c->min_active, min(Mmid, Mn));
-  c->max_active = max(c->max_active, Mn);
+  c->host_decided = decided + (uint32_t)Wmid;
+  c->barriers = barriers;
+  c->kills = kills0 + Wmid + W;
+  c->forks = forks0 + k;
+  c->min_active = min(mina, min(Mmid, Mn));
+  c->max_active = max(maxa, Mn);
   if (!nxt.done) {
-    c->edges_scanned += edges;
-    c->frontier_total += count;
+    c->edges_scanned = es0 + edges;
+    c->frontier_total = ft0 + count;
   }
   // every barrier while the first half of the trace has room, resize events always
-  const int32_t t_us = (int32_t)((gtime() - c->t_start) / 1000ull);
-  if (Wmid > 0 && c->log_n < (uint32_t)kLogCap) {  // the host kills of the interval
-    c->log[c->log_n] = LogRec{c->barriers, t_us, M, 0, Wmid, Mmid, 0, (int32_t)edges};
-    c->log_n += 1u;
+  const int32_t t_us = (int32_t)((gtime() - t_start) / 1000ull);
+  if (Wmid > 0 && log_n < (uint32_t)kLogCap) {  // the host kills of the interval
+    c->log[log_n] = LogRec{barriers, t_us, M, 0, Wmid, Mmid, 0, (int32_t)edges};
+    ++log_n;
   }
-  if (c->log_n < (uint32_t)kLogCap && (c->log_n < (uint32_t)kLogCap / 2u || (k | W | spawned) != 0)) {
-    c->log[c->log_n] = LogRec{c->barriers, t_us, Mmid, k, W, Mn, spawned, (int32_t)edges};
-    c->log_n += 1u;
+  if (log_n < (uint32_t)kLogCap && (log_n < (uint32_t)kLogCap / 2u || (k | W | spawned) != 0)) {
+    c->log[log_n] = LogRec{barriers, t_us, Mmid, k, W, Mn, spawned, (int32_t)edges};
+    ++log_n;
   }
+  c->log_n = log_n;
   nxt.M = Mn;
   nxt.doom = (uint32_t)Mmid;
   c->iv = nxt;
   if (nxt.done) {
     st_relaxed(&c->done, 1u);
-    const uint32_t e = ld_relaxed(&c->err);
-    publish_stats(p, e ? (int)e : (ld_relaxed(&c->ovf) ? (int)ERR_OVERFLOW : 0));
+    publish_stats(p, err ? (int)err : (ld_relaxed(&c->ovf) ? (int)ERR_OVERFLOW : 0));
   }
   return nxt;
 }
@@ -468,9 +470,10 @@ __device__ __forceinline__ bool resizing_barrier(const Params &p, CtaShared &cs)
   if (threadIdx.x == 0) {
     Ctl *c = p.ctl;
     const Interval cur = cs.iv;
-    // offer_kill: a CTA inside the host's kill target leaves as soon as it arrives (read
-    // before arriving, so the releaser's closed target -- never higher -- includes it)
-    bool leave = p.coop && doomed(ld_relaxed64(&c->kill_target), cur.epoch, cs.id);
+    // offer_kill: a CTA inside the host's kill target leaves as soon as it sees the target
+    // while waiting (it has arrived, and the target is only ever lowered until the
+    // releaser stamps it closed, so the closed target includes it)
+    bool leave = false;
     const uint32_t old = atom_add_acq_rel(&c->arrive.v, 1u);
     bool ok = true;
     if (old == (uint32_t)(cur.M - 1) + p.extra_wait) {
@@ -478,7 +481,7 @@ __device__ __forceinline__ bool resizing_barrier(const Params &p, CtaShared &cs)
       st_relaxed(&c->arrive.v, 0u);
       st_release(&c->epoch.v, cur.epoch + 1u);
       cs.iv = nxt;
-    } else if (!leave) {
+    } else {
       const int w = wait_release(p, cur.epoch, p.coop ? cs.id : -1);
       ok = w != 0;
       if (w == 1) cs.iv = read_iv(c);

@@ -68,6 +68,13 @@ def emulate_warp(qo, qs, F, Etot, E0, E1, wb=None):
     if wb is None:
         wb = find_entry(qo, F, E0)
     win = [load(qo, qs, F, Etot, wb + l) for l in range(32)]
+    while True:  # catch-up slides until lane 0 holds the entry containing E0
+        ended = ballot(np.array([w[1] <= E0 for w in win]))
+        if not ended:
+            break
+        n = popc(ended)
+        wb += n
+        win = [win[(l + n) & 31] if l + n < 32 else load(qo, qs, F, Etot, wb + l) for l in range(32)]
     c = E0
     while c < E1:
         ended = ballot(np.array([w[1] <= c for w in win]))
@@ -105,11 +112,12 @@ def check_frontier_chunks(degs, rng):
     qx = index_chunks(qo, degs, nchunks)
     assert np.all(qx >= 0)
     assert np.array_equal(qx, owner[np.arange(nchunks) * CHUNK])
-    for mult in (1, 3, 8):
+    for mult in (1, 3, 8, 16):  # chunks of 32*mult edges, started from the 128-edge index
+        units = (Etot + 31) // 32
         seen = np.zeros(Etot, dtype=np.int64)
-        for j in rng.permutation((nchunks + mult - 1) // mult):
-            c0, c1 = j * CHUNK * mult, min((j + 1) * CHUNK * mult, Etot)
-            for e, pos in emulate_warp(qo, qs, F, Etot, c0, c1, wb=int(qx[j * mult])):
+        for j in rng.permutation((units + mult - 1) // mult):
+            c0, c1 = j * 32 * mult, min((j + 1) * 32 * mult, Etot)
+            for e, pos in emulate_warp(qo, qs, F, Etot, c0, c1, wb=int(qx[c0 // CHUNK])):
                 u = owner[e]
                 assert pos == qs[u] + (e - qo[u])
                 seen[e] += 1
