@@ -159,16 +159,100 @@ __device__ __forceinline__ bool row_of(const Params &p, uint32_t v, uint32_t &rs
   return true;
 }
 
-constexpr int kUnroll = 4;  // 32-edge chunks a warp has in flight per iteration
+constexpr int kUnroll = 4;  // 32-edge groups a warp handles per iteration
+
+// Per-warp landing buffer of the column stream: two slots of kUnroll x 32 edges, each
+// edge's column (and, for SSSP, its weight and its source's distance).  While a warp
+// claims the targets of one slot, the asynchronous copies of the next 128 edges fill the
+// other, so the DRAM latency of the column stream overlaps the L2 round trips of the
+// claim.  Every lane copies and later reads only its own words of a slot.
+constexpr int kStages = 2;  // landing slots: copies run kStages - 1 iterations ahead
+struct Prefetch {
+  uint32_t col[kStages][kUnroll][32];
+  uint32_t w[kStages][kUnroll][32];
+  uint32_t du[kStages][kUnroll][32];
+};
+static_assert(kDefaultWorkerWarps * (sizeof(WarpStage) + sizeof(Prefetch)) <= (size_t)kReserveSmem,
+              "per-warp staging must fit in a traversal CTA's dynamic shared memory");
+
+__device__ __forceinline__ void cp_async4(void *sdst, const void *gsrc) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Drop the window's entries that end at or before edge x (32 at most per call); true if
+// any did.  Once it returns false, lane 0 holds the entry containing x.
+template <int MODE>
+__device__ __forceinline__ bool slide(const Params &p, const uint32_t *qo, const uint32_t *qs, const uint32_t *qv,
+                                      uint32_t F, uint32_t Etot, uint32_t x, Window &w, uint32_t &wb,
+                                      unsigned lane) {
+  const unsigned ended = __ballot_sync(kFull, w.end <= x);
+  if (!ended) return false;
+  const unsigned n = (unsigned)__popc(ended);
+  wb += n;
+  const unsigned srcl = (lane + n) & 31u;
+  Window t;
+  t.off = __shfl_sync(kFull, w.off, srcl);
+  t.end = __shfl_sync(kFull, w.end, srcl);
+  t.start = __shfl_sync(kFull, w.start, srcl);
+  if (MODE == MODE_SSSP) {
+    t.u = __shfl_sync(kFull, w.u, srcl);
+    t.du = __shfl_sync(kFull, w.du, srcl);
+  }
+  if (lane + n < 32u) w = t;
+  else load_entry<MODE>(p, qo, qs, qv, F, Etot, wb + lane, w);
+  return true;
+}
+
+// The index arithmetic of the kUnroll groups starting at edge c (window slide, source
+// entry of each lane's edge) and the start of their column (and weight) copies into
+// slot sb of the landing buffer.
+template <int MODE>
+__device__ __forceinline__ void issue_groups(const Params &p, const uint32_t *qo, const uint32_t *qs,
+                                             const uint32_t *qv, uint32_t F, uint32_t Etot, uint32_t c,
+                                             uint32_t E1, Window &w, uint32_t &wb, Prefetch &pf, int sb,
+                                             unsigned lane, unsigned lm_le) {
+#pragma unroll
+  for (int u = 0; u < kUnroll; ++u) {
+    const uint32_t cu = c + 32u * (uint32_t)u;
+    if (cu >= E1) break;  // warp-uniform
+    // every entry holds at least one edge, so one slide covers a 32-edge step
+    slide<MODE>(p, qo, qs, qv, F, Etot, cu, w, wb, lane);
+    // entries starting strictly inside [cu, cu+32) -> source entry of each lane's edge
+    const uint32_t rel = w.off - cu;
+    const unsigned bit = (lane != 0u && rel < 32u) ? (1u << rel) : 0u;
+    const unsigned bits = __reduce_or_sync(kFull, bit);
+    const unsigned idx = (unsigned)__popc(bits & lm_le);
+    const uint32_t s0 = __shfl_sync(kFull, w.start, idx);
+    const uint32_t o0 = __shfl_sync(kFull, w.off, idx);
+    uint32_t du = 0u;
+    if (MODE == MODE_SSSP) du = __shfl_sync(kFull, w.du, idx);
+    const uint32_t e = cu + lane;
+    if (e < E1) {
+      const uint32_t pos = s0 + (e - o0);
+      cp_async4(&pf.col[sb][u][lane], p.col + pos);
+      if (MODE == MODE_SSSP) {
+        cp_async4(&pf.w[sb][u][lane], p.w + pos);
+        pf.du[sb][u][lane] = du;
+      }
+    }
+  }
+  cp_async_commit();
+}
 
 // Expand edges [c0, c1) of the interval's edge space; entry wb of the input queue holds
-// edge c0.  kUnroll 32-edge groups at a time: first the index arithmetic of all groups
-// (window slides, source entry per lane), then all column loads, then all state loads,
-// so every lane keeps kUnroll independent memory chains in flight.
+// edge c0.  Software-pipelined over iterations of kUnroll 32-edge groups: the copies of
+// iteration i+1 are started, then iteration i's targets are claimed, so every lane keeps
+// the next kUnroll column loads in flight while it works on the current ones.
 template <int MODE>
 __device__ __forceinline__ void expand_range(const Params &p, const Interval &iv, uint32_t c0, uint32_t c1,
-                                             uint32_t wb, WarpStage &stage, uint32_t &staged, bool &bad,
-                                             bool &ovf, uint32_t &nreach, uint64_t &ereach) {
+                                             uint32_t wb, WarpStage &stage, Prefetch &pf, uint32_t &staged,
+                                             bool &bad, bool &ovf, uint32_t &nreach, uint64_t &ereach) {
   const unsigned lane = threadIdx.x & 31u;
   const uint32_t Etot = iv.edges;
   const uint32_t F = iv.count;
@@ -183,68 +267,31 @@ __device__ __forceinline__ void expand_range(const Params &p, const Interval &iv
 
   Window w;
   load_entry<MODE>(p, qo, qs, qv, F, Etot, wb + lane, w);
-  // the index names the entry holding the 128-edge unit boundary at or before c0; slide
-  // (32 entries at most per step) until lane 0 holds the entry containing c0
-  for (;;) {
-    const unsigned ended = __ballot_sync(kFull, w.end <= c0);
-    if (!ended) break;
-    const unsigned n = (unsigned)__popc(ended);
-    wb += n;
-    const unsigned srcl = (lane + n) & 31u;
-    Window s;
-    s.off = __shfl_sync(kFull, w.off, srcl);
-    s.end = __shfl_sync(kFull, w.end, srcl);
-    s.start = __shfl_sync(kFull, w.start, srcl);
-    if (MODE == MODE_SSSP) {
-      s.u = __shfl_sync(kFull, w.u, srcl);
-      s.du = __shfl_sync(kFull, w.du, srcl);
-    }
-    if (lane + n < 32u) w = s;
-    else load_entry<MODE>(p, qo, qs, qv, F, Etot, wb + lane, w);
+  // the index names the entry holding the 128-edge unit boundary at or before c0, up to
+  // 127 entries back: catch up until lane 0 holds the entry containing c0
+  while (slide<MODE>(p, qo, qs, qv, F, Etot, c0, w, wb, lane)) {
   }
-
-  for (uint32_t c = c0; c < E1; c += 32u * kUnroll) {
-    uint32_t pos[kUnroll], du[kUnroll];
-    bool val[kUnroll];
+  // prologue: the first kStages - 1 iterations' copies (an empty group past the end, so
+  // that every iteration below commits exactly one group)
+  uint32_t ci = c0;
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const uint32_t cu = c + 32u * (uint32_t)u;
-      val[u] = false;
-      pos[u] = 0u;
-      du[u] = 0u;
-      if (cu >= E1) continue;  // warp-uniform
-      // slide the window so that lane 0 holds the entry containing edge cu
-      const unsigned ended = __ballot_sync(kFull, w.end <= cu);
-      if (ended) {
-        const unsigned n = (unsigned)__popc(ended);
-        wb += n;
-        const unsigned srcl = (lane + n) & 31u;
-        Window s;
-        s.off = __shfl_sync(kFull, w.off, srcl);
-        s.end = __shfl_sync(kFull, w.end, srcl);
-        s.start = __shfl_sync(kFull, w.start, srcl);
-        if (MODE == MODE_SSSP) {
-          s.u = __shfl_sync(kFull, w.u, srcl);
-          s.du = __shfl_sync(kFull, w.du, srcl);
-        }
-        if (lane + n < 32u) w = s;
-        else load_entry<MODE>(p, qo, qs, qv, F, Etot, wb + lane, w);
-      }
-      // entries starting strictly inside [cu, cu+32) -> source entry of each lane's edge
-      const uint32_t rel = w.off - cu;
-      const unsigned bit = (lane != 0u && rel < 32u) ? (1u << rel) : 0u;
-      const unsigned bits = __reduce_or_sync(kFull, bit);
-      const unsigned idx = (unsigned)__popc(bits & lm_le);
-      const uint32_t s0 = __shfl_sync(kFull, w.start, idx);
-      const uint32_t o0 = __shfl_sync(kFull, w.off, idx);
-      if (MODE == MODE_SSSP) du[u] = __shfl_sync(kFull, w.du, idx);
-      const uint32_t e = cu + lane;
-      val[u] = e < E1;
-      pos[u] = s0 + (e - o0);
-    }
+  for (int k = 0; k < kStages - 1; ++k, ci += 32u * kUnroll) {
+    if (ci < E1) issue_groups<MODE>(p, qo, qs, qv, F, Etot, ci, E1, w, wb, pf, k, lane, lm_le);
+    else cp_async_commit();
+  }
+  int sb = 0, sn = kStages - 1;
+  for (uint32_t c = c0; c < E1; c += 32u * kUnroll, ci += 32u * kUnroll) {
+    if (ci < E1) issue_groups<MODE>(p, qo, qs, qv, F, Etot, ci, E1, w, wb, pf, sn, lane, lm_le);
+    else cp_async_commit();
+    cp_async_wait<kStages - 1>();  // this iteration's slot has landed; later ones stay in flight
+    bool val[kUnroll];
     uint32_t vv[kUnroll];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) vv[u] = val[u] ? (uint32_t)__ldg(p.col + pos[u]) : 0xFFFFFFFFu;
+    for (int u = 0; u < kUnroll; ++u) {
+      val[u] = c + 32u * (uint32_t)u + lane < E1;
+      vv[u] = val[u] ? pf.col[sb][u][lane] : 0xFFFFFFFFu;
+    }
+
     if (MODE == MODE_BFS) {
       uint32_t word[kUnroll];
 #pragma unroll
@@ -255,6 +302,16 @@ __device__ __forceinline__ void expand_range(const Params &p, const Interval &iv
         }
         word[u] = val[u] ? *(p.visited + (vv[u] >> 5)) : 0xFFFFFFFFu;
       }
+      // Row bounds of every candidate the bitmap word shows unvisited are read before
+      // its atomicOr, not after, so the two round trips overlap; a candidate that then
+      // loses the claim race wasted two cached loads.
+      int32_t ra[kUnroll], rb[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const bool cand = val[u] && (word[u] & (1u << (vv[u] & 31u))) == 0u;
+        ra[u] = cand ? __ldg(p.row_off + vv[u]) : 0;
+        rb[u] = cand ? __ldg(p.row_off + vv[u] + 1) : 0;
+      }
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) {
         const uint32_t m = 1u << (vv[u] & 31u);
@@ -264,17 +321,27 @@ __device__ __forceinline__ void expand_range(const Params &p, const Interval &iv
         bool push = false;
         if (claim) {
           p.level[vv[u]] = (int32_t)next_level;
-          if (row_of(p, vv[u], rs, deg)) push = deg > 0u;
-          else bad = true;
+          if (ra[u] < 0 || rb[u] < ra[u] || (uint32_t)rb[u] > p.E) bad = true;
+          else { rs = (uint32_t)ra[u]; deg = (uint32_t)(rb[u] - ra[u]); push = deg > 0u; }
           nreach += 1u;
           ereach += deg;
         }
         stage_push<MODE>(p, out, stage, staged, push, vv[u], rs, deg, lane);
       }
     } else {
-      uint32_t wt[kUnroll], dv[kUnroll];
+      // SSSP's claim is a chain of three dependent round trips (atomicMin, stamp,
+      // row_off), so it runs in phases across the kUnroll groups -- all atomicMins,
+      // then all stamp claims, then all row reads, then the enqueues -- and the groups'
+      // chains overlap.  (For BFS, phasing measured slower than a claim kept next to its
+      // enqueue; for SSSP, reading rows speculatively measured slower than phasing.)
+      bool push[kUnroll];
+      uint32_t rs[kUnroll], deg[kUnroll];
+      uint32_t wt[kUnroll], du[kUnroll], dv[kUnroll], old[kUnroll];
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u) wt[u] = val[u] ? __ldg(p.w + pos[u]) : 0u;
+      for (int u = 0; u < kUnroll; ++u) {
+        wt[u] = val[u] ? pf.w[sb][u][lane] : 0u;
+        du[u] = val[u] ? pf.du[sb][u][lane] : 0u;
+      }
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) {
         if (val[u] && vv[u] >= V) {
@@ -283,37 +350,45 @@ __device__ __forceinline__ void expand_range(const Params &p, const Interval &iv
         }
         dv[u] = val[u] ? *(volatile const uint32_t *)(p.dist + vv[u]) : 0u;
       }
+      const uint32_t tag = next_level + 1u;  // stamp of "queued for the next round"
+      bool imp[kUnroll];
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) {
-        bool push = false;
-        uint32_t rs = 0u, deg = 0u;
+        imp[u] = false;
+        old[u] = 0u;
         if (val[u]) {
           const uint64_t nd64 = (uint64_t)du[u] + (uint64_t)wt[u];
-          if (nd64 >= 0xFFFFFFFFull) {
-            ovf = true;
-          } else {
-            const uint32_t nd = (uint32_t)nd64;
-            uint32_t old = 0u;
-            if (nd < dv[u] && nd < (old = atomicMin(p.dist + vv[u], nd))) {
-              const uint32_t tag = next_level + 1u;  // stamp of "queued for the next round"
-              uint32_t *sv = p.stamp + vv[u];
-              if (*(volatile uint32_t *)sv != tag && atomicExch(sv, tag) != tag) {
-                if (row_of(p, vv[u], rs, deg)) push = deg > 0u;
-                else bad = true;
-              } else if (old == 0xFFFFFFFFu) {
-                row_of(p, vv[u], rs, deg);
-              }
-              if (old == 0xFFFFFFFFu) {  // first time this vertex is reached
-                nreach += 1u;
-                ereach += deg;
-              }
-              if (!push) deg = 0u;
-            }
+          if (nd64 >= 0xFFFFFFFFull) ovf = true;
+          else if ((uint32_t)nd64 < dv[u]) {
+            old[u] = atomicMin(p.dist + vv[u], (uint32_t)nd64);
+            imp[u] = (uint32_t)nd64 < old[u];
           }
         }
-        stage_push<MODE>(p, out, stage, staged, push, vv[u], rs, deg, lane);
       }
+      uint32_t st[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) st[u] = imp[u] ? *(volatile uint32_t *)(p.stamp + vv[u]) : tag;
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) push[u] = imp[u] && st[u] != tag && atomicExch(p.stamp + vv[u], tag) != tag;
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        rs[u] = 0u;
+        deg[u] = 0u;
+        const bool first = imp[u] && old[u] == 0xFFFFFFFFu;  // first time this vertex is reached
+        if (push[u] || first) {
+          if (!row_of(p, vv[u], rs[u], deg[u])) bad = true;
+        }
+        if (first) {
+          nreach += 1u;
+          ereach += deg[u];
+        }
+        push[u] = push[u] && deg[u] > 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) stage_push<MODE>(p, out, stage, staged, push[u], vv[u], rs[u], deg[u], lane);
     }
+    sb = sb + 1 == kStages ? 0 : sb + 1;
+    sn = sn + 1 == kStages ? 0 : sn + 1;
   }
 }
 
@@ -325,7 +400,7 @@ __device__ __forceinline__ void expand_range(const Params &p, const Interval &iv
 // over the rest.  The enqueue built a chunk index (entry holding each unit's first
 // edge), so a chunk starts without any search.
 template <int MODE, int NW>
-__device__ void expand(const Params &p, const Interval &iv, int32_t id, WarpStage &stage) {
+__device__ void expand(const Params &p, const Interval &iv, int32_t id, WarpStage &stage, Prefetch &pf) {
   const unsigned lane = threadIdx.x & 31u;
   const uint32_t Etot = iv.edges;
   const uint32_t GW = (uint32_t)iv.M * NW;
@@ -351,7 +426,7 @@ __device__ void expand(const Params &p, const Interval &iv, int32_t id, WarpStag
     }
     const uint32_t c0 = j * csize;
     const uint32_t c1 = min(c0 + csize, Etot);
-    expand_range<MODE>(p, iv, c0, c1, qx[c0 / kIndexEdges], stage, staged, bad, ovf, nreach, ereach);
+    expand_range<MODE>(p, iv, c0, c1, qx[c0 / kIndexEdges], stage, pf, staged, bad, ovf, nreach, ereach);
     j = __shfl_sync(kFull, jn, 0);
   }
   if (staged) stage_flush<MODE>(p, out, stage, staged, lane);
@@ -433,13 +508,14 @@ __device__ __forceinline__ void scheduler_warp(const Params &p, const volatile i
 }
 
 template <int MODE, int NW>
-__device__ __forceinline__ void worker_loop(const Params &p, CtaShared &cs, WarpStage *stages) {
+__device__ __forceinline__ void worker_loop(const Params &p, CtaShared &cs, WarpStage *stages, Prefetch *pfs) {
   WarpStage &stage = stages[threadIdx.x >> 5];
+  Prefetch &pf = pfs[threadIdx.x >> 5];
   for (;;) {
     const Interval iv = cs.iv;
     const int32_t id = cs.id;
     if (iv.done || id >= iv.M) return;  // finished, or left through offer_kill
-    if (MODE != MODE_BARRIER) expand<MODE, NW>(p, iv, id, stage);
+    if (MODE != MODE_BARRIER) expand<MODE, NW>(p, iv, id, stage, pf);
     if (!resizing_barrier<MODE, NW>(p, cs)) return;
   }
 }
@@ -468,7 +544,9 @@ __device__ __forceinline__ void traverse_body(const Params &p, bool master, CtaS
     if (p.coop && cs.id == 0 && threadIdx.x == NW * 32) scheduler_warp<MODE, NW>(p, &cs.workers_left);
     return;
   }
-  worker_loop<MODE, NW>(p, cs, reinterpret_cast<WarpStage *>(dyn));
+  // dynamic shared memory: NW enqueue stages, then NW landing buffers
+  worker_loop<MODE, NW>(p, cs, reinterpret_cast<WarpStage *>(dyn),
+                        reinterpret_cast<Prefetch *>(dyn + NW * sizeof(WarpStage)));
   if (threadIdx.x == 0) *(volatile int32_t *)&cs.workers_left = 1;
 }
 

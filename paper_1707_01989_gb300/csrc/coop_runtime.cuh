@@ -40,8 +40,10 @@ namespace coopdev {
 constexpr int kDefaultWorkerWarps = 31;
 constexpr int kMaxCtas = 2048;              // admission slot table; N <= kMaxCtas
 constexpr int kLogCap = 4096;               // resize-log records per run
-constexpr int kReserveSmem = 116 * 1024;    // dynamic smem of a traversal CTA
-constexpr int kCorunnerSmem = 116 * 1024;   // dynamic smem of a co-runner CTA (sum > SM capacity)
+// A traversal CTA and a co-runner CTA each take more than half of an SM's 228 KB of
+// shared memory, so neither can share an SM with the other (or with its own kind).
+constexpr int kReserveSmem = 120 * 1024;    // dynamic smem of a traversal CTA (staging + landing buffers)
+constexpr int kCorunnerSmem = 116 * 1024;   // dynamic smem of a co-runner CTA
 constexpr uint64_t kEntryGatherNs = 20000;  // master waits this long for its launch to register
 constexpr uint32_t kIndexEdges = 128;       // granularity of the chunk index (edges per unit)
 constexpr uint32_t kChunkUnitsMax = 16;     // a work chunk spans 1..16 32-edge units, sized to the frontier
