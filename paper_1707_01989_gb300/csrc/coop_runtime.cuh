@@ -354,11 +354,36 @@ __device__ __forceinline__ bool wait_epoch_at_least(const Params &p, uint32_t e)
 template <int MODE, int NW>
 __device__ void spawn_forks(const Params &p, uint32_t n);
 
+// Releaser-private books of one release, stored after the epoch word is released: no
+// waiter reads them, and this thread's next arrival (a release) orders them before the
+// next releaser's loads.
+struct Books {
+  uint32_t admitted;
+  int32_t barriers, kills, forks, min_active, max_active;
+  unsigned long long edges_scanned, frontier_total;
+  uint32_t log_n;
+  bool has_kill, has_rec;  // trace records to append: the host kills, the resize
+  LogRec kill_rec, rec;
+  int32_t status;  // final status when the traversal is over, else 1
+};
+
 template <int MODE, int NW>
-__device__ __forceinline__ Interval release_step(const Params &p, const Interval cur) {
+__device__ __forceinline__ Interval release_step(const Params &p, const Interval cur, Books &bk) {
   Ctl *c = p.ctl;
-  // Everything the release needs is loaded first, in one batch of independent loads:
-  // the output queue's counters and the releaser-private books.
+  const int32_t M = cur.M;
+  // (5) of the query barrier for the host's requests: close this interval's kill target.
+  // CTAs with ids >= Mmid leave (those that saw it while waiting already left; the
+  // others leave right after this release).  The word is stamped closed for this epoch
+  // even when no target was set, so that a scheduler update computed before this
+  // release can no longer land on this epoch; a lower open target is then put back.
+  // Issued first so that its round trip overlaps the loads below.
+  unsigned long long closed = 0ull, kt = 0ull;
+  if (p.coop) {
+    closed = ((unsigned long long)cur.epoch << 32) | kTargetClosed;
+    kt = atomicExch(&c->kill_target, closed | (unsigned long long)(uint32_t)M);
+  }
+  // Everything else the release needs, in one batch of independent loads: the output
+  // queue's counters and the releaser-private books.
   const uint32_t out = cur.sel ^ 1u;
   const unsigned long long packed = (MODE == MODE_BARRIER) ? 0ull : c->qctr[out];
   const uint32_t A = c->admitted;
@@ -369,19 +394,9 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
   uint32_t log_n = c->log_n;
   const uint32_t err = ld_relaxed(&c->err);
   const uint32_t R = p.coop ? ld_relaxed(&c->join_ticket.v) : 0u;
-  const int32_t M = cur.M;
-  // (5) of the query barrier for the host's requests: close this interval's kill target.
-  // CTAs with ids >= Mmid leave (those that saw it while waiting already left; the
-  // others leave right after this release).  The word is stamped closed for this epoch
-  // even when no target was set, so that a scheduler update computed before this
-  // release can no longer land on this epoch; a lower open target is then put back.
+  const uint64_t now = gtime();
   int32_t Mmid = M;
-  unsigned long long closed = 0ull;
-  if (p.coop) {
-    closed = ((unsigned long long)cur.epoch << 32) | kTargetClosed;
-    const unsigned long long kt = atomicExch(&c->kill_target, closed | (unsigned long long)(uint32_t)M);
-    if ((uint32_t)(kt >> 32) == cur.epoch) Mmid = min(M, max(1, (int32_t)(kt & 0x7FFFFFFFull)));
-  }
+  if (p.coop && (uint32_t)(kt >> 32) == cur.epoch) Mmid = min(M, max(1, (int32_t)(kt & 0x7FFFFFFFull)));
   if (Mmid < M) st_relaxed64(&c->kill_target, closed | (unsigned long long)(uint32_t)Mmid);
 
   Interval nxt = cur;
@@ -432,36 +447,49 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
     const uint32_t idv = (uint32_t)(Mmid + i);
     st_relaxed64(&c->slot[t % kMaxCtas], slot_pack(nxt.epoch, idv >= (uint32_t)Mn, idv, t));
   }
-  c->admitted = A + (uint32_t)k;
+  // read by the scheduler warp together with the interval: published with it
   c->host_decided = decided + (uint32_t)Wmid;
-  c->barriers = barriers;
-  c->kills = kills0 + Wmid + W;
-  c->forks = forks0 + k;
-  c->min_active = min(mina, min(Mmid, Mn));
-  c->max_active = max(maxa, Mn);
-  if (!nxt.done) {
-    c->edges_scanned = es0 + edges;
-    c->frontier_total = ft0 + count;
-  }
-  // every barrier while the first half of the trace has room, resize events always
-  const int32_t t_us = (int32_t)((gtime() - t_start) / 1000ull);
-  if (Wmid > 0 && log_n < (uint32_t)kLogCap) {  // the host kills of the interval
-    c->log[log_n] = LogRec{barriers, t_us, M, 0, Wmid, Mmid, 0, (int32_t)edges};
-    ++log_n;
-  }
-  if (log_n < (uint32_t)kLogCap && (log_n < (uint32_t)kLogCap / 2u || (k | W | spawned) != 0)) {
-    c->log[log_n] = LogRec{barriers, t_us, Mmid, k, W, Mn, spawned, (int32_t)edges};
-    ++log_n;
-  }
-  c->log_n = log_n;
   nxt.M = Mn;
   nxt.doom = (uint32_t)Mmid;
   c->iv = nxt;
-  if (nxt.done) {
-    st_relaxed(&c->done, 1u);
-    publish_stats(p, err ? (int)err : (ld_relaxed(&c->ovf) ? (int)ERR_OVERFLOW : 0));
-  }
+  if (nxt.done) st_relaxed(&c->done, 1u);
+
+  bk.admitted = A + (uint32_t)k;
+  bk.barriers = barriers;
+  bk.kills = kills0 + Wmid + W;
+  bk.forks = forks0 + k;
+  bk.min_active = min(mina, min(Mmid, Mn));
+  bk.max_active = max(maxa, Mn);
+  bk.edges_scanned = nxt.done ? es0 : es0 + edges;
+  bk.frontier_total = nxt.done ? ft0 : ft0 + count;
+  // every barrier while the first half of the trace has room, resize events always
+  const int32_t t_us = (int32_t)((now - t_start) / 1000ull);
+  bk.has_kill = Wmid > 0 && log_n < (uint32_t)kLogCap;  // the host kills of the interval
+  bk.kill_rec = LogRec{barriers, t_us, M, 0, Wmid, Mmid, 0, (int32_t)edges};
+  const uint32_t ln = log_n + (bk.has_kill ? 1u : 0u);
+  bk.has_rec = ln < (uint32_t)kLogCap && (ln < (uint32_t)kLogCap / 2u || (k | W | spawned) != 0);
+  bk.rec = LogRec{barriers, t_us, Mmid, k, W, Mn, spawned, (int32_t)edges};
+  bk.log_n = log_n;
+  bk.status = nxt.done ? (err ? (int)err : (ld_relaxed(&c->ovf) ? (int)ERR_OVERFLOW : 0)) : 1;
   return nxt;
+}
+
+// The second half of a release, after the epoch word has been released.
+__device__ __forceinline__ void release_books(const Params &p, const Books &bk) {
+  Ctl *c = p.ctl;
+  c->admitted = bk.admitted;
+  c->barriers = bk.barriers;
+  c->kills = bk.kills;
+  c->forks = bk.forks;
+  c->min_active = bk.min_active;
+  c->max_active = bk.max_active;
+  c->edges_scanned = bk.edges_scanned;
+  c->frontier_total = bk.frontier_total;
+  uint32_t ln = bk.log_n;
+  if (bk.has_kill) c->log[ln++] = bk.kill_rec;
+  if (bk.has_rec) c->log[ln++] = bk.rec;
+  c->log_n = ln;
+  if (bk.status != 1) publish_stats(p, bk.status);
 }
 
 // The resizing global barrier, called by all worker threads of an active CTA.
@@ -479,9 +507,11 @@ __device__ __forceinline__ bool resizing_barrier(const Params &p, CtaShared &cs)
     const uint32_t old = atom_add_acq_rel(&c->arrive.v, 1u);
     bool ok = true;
     if (old == (uint32_t)(cur.M - 1) + p.extra_wait) {
-      const Interval nxt = release_step<MODE, NW>(p, cur);
+      Books bk;
+      const Interval nxt = release_step<MODE, NW>(p, cur, bk);
       st_relaxed(&c->arrive.v, 0u);
       st_release(&c->epoch.v, cur.epoch + 1u);
+      release_books(p, bk);
       cs.iv = nxt;
     } else {
       const int w = wait_release(p, cur.epoch, p.coop ? cs.id : -1);
