@@ -18,8 +18,9 @@
 //    each lane its source entry, so column loads are coalesced;
 //  * BFS claims a vertex with an atomicOr on a 1-bit-per-vertex visited bitmap (checked
 //    first with a plain load; stale reads only cost an extra atomic), writes its level
-//    and enqueues it if its out-degree is non-zero; SSSP relaxes with atomicMin and
-//    enqueues a lowered vertex once per round through a round stamp.
+//    and enqueues it if its out-degree is non-zero; SSSP keeps (distance, round stamp)
+//    of a vertex in one 64-bit word, so a single 64-bit atomicMin both lowers the
+//    distance and tells whether the vertex is already queued for the next round.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -61,7 +62,7 @@ __device__ __forceinline__ void load_entry(const Params &p, const uint32_t *qo, 
     w.end = (i + 1u < F) ? qo[i + 1u] : Etot;
     if (MODE == MODE_SSSP) {
       w.u = qv[i];
-      w.du = *(volatile const uint32_t *)(p.dist + w.u);
+      w.du = (uint32_t)(*(volatile const unsigned long long *)(p.ds + w.u) >> 32);
     }
   } else {
     w.off = 0xFFFFFFFFu;
@@ -329,14 +330,18 @@ __device__ __forceinline__ void expand_range(const Params &p, const Interval &iv
         stage_push<MODE>(p, out, stage, staged, push, vv[u], rs, deg, lane);
       }
     } else {
-      // SSSP's claim is a chain of three dependent round trips (atomicMin, stamp,
-      // row_off), so it runs in phases across the kUnroll groups -- all atomicMins,
-      // then all stamp claims, then all row reads, then the enqueues -- and the groups'
-      // chains overlap.  (For BFS, phasing measured slower than a claim kept next to its
-      // enqueue; for SSSP, reading rows speculatively measured slower than phasing.)
+      // Relaxation on the packed word ds[v] = (dist << 32) | stamp.  One 64-bit atomicMin
+      // with (nd << 32) | tag lowers the distance exactly when nd < dist (stamps only grow,
+      // so an equal distance never rewrites the word), and the old word it returns says
+      // whether this relaxation lowered it (nd < old dist) and whether the vertex was
+      // already queued for the next round (old stamp == tag): the first lowering of a
+      // round enqueues, later ones find the vertex queued and its expansion reads the
+      // distance then current.  The phases run across the kUnroll groups -- all
+      // pre-check loads, then all atomics, then all row reads -- so their chains overlap.
       bool push[kUnroll];
       uint32_t rs[kUnroll], deg[kUnroll];
-      uint32_t wt[kUnroll], du[kUnroll], dv[kUnroll], old[kUnroll];
+      uint32_t wt[kUnroll], du[kUnroll], dv[kUnroll];
+      unsigned long long old[kUnroll];
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) {
         wt[u] = val[u] ? pf.w[sb][u][lane] : 0u;
@@ -348,33 +353,29 @@ __device__ __forceinline__ void expand_range(const Params &p, const Interval &iv
           bad = true;
           val[u] = false;
         }
-        dv[u] = val[u] ? *(volatile const uint32_t *)(p.dist + vv[u]) : 0u;
+        dv[u] = val[u] ? (uint32_t)(*(volatile const unsigned long long *)(p.ds + vv[u]) >> 32) : 0u;
       }
       const uint32_t tag = next_level + 1u;  // stamp of "queued for the next round"
       bool imp[kUnroll];
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) {
         imp[u] = false;
-        old[u] = 0u;
+        old[u] = 0ull;
         if (val[u]) {
           const uint64_t nd64 = (uint64_t)du[u] + (uint64_t)wt[u];
           if (nd64 >= 0xFFFFFFFFull) ovf = true;
           else if ((uint32_t)nd64 < dv[u]) {
-            old[u] = atomicMin(p.dist + vv[u], (uint32_t)nd64);
-            imp[u] = (uint32_t)nd64 < old[u];
+            old[u] = atomicMin(p.ds + vv[u], (nd64 << 32) | (unsigned long long)tag);
+            imp[u] = (uint32_t)nd64 < (uint32_t)(old[u] >> 32);
           }
         }
       }
-      uint32_t st[kUnroll];
-#pragma unroll
-      for (int u = 0; u < kUnroll; ++u) st[u] = imp[u] ? *(volatile uint32_t *)(p.stamp + vv[u]) : tag;
-#pragma unroll
-      for (int u = 0; u < kUnroll; ++u) push[u] = imp[u] && st[u] != tag && atomicExch(p.stamp + vv[u], tag) != tag;
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) {
         rs[u] = 0u;
         deg[u] = 0u;
-        const bool first = imp[u] && old[u] == 0xFFFFFFFFu;  // first time this vertex is reached
+        push[u] = imp[u] && (uint32_t)old[u] != tag;
+        const bool first = imp[u] && (uint32_t)(old[u] >> 32) == 0xFFFFFFFFu;  // first time reached
         if (push[u] || first) {
           if (!row_of(p, vv[u], rs[u], deg[u])) bad = true;
         }
@@ -507,6 +508,13 @@ __device__ __forceinline__ void scheduler_warp(const Params &p, const volatile i
   }
 }
 
+template <int NW>
+__device__ __forceinline__ void copy_dist(const Params &p, int32_t id, int32_t M) {
+  const size_t V = (size_t)p.V;
+  const size_t lo = V * (size_t)id / (size_t)M, hi = V * (size_t)(id + 1) / (size_t)M;
+  for (size_t i = lo + threadIdx.x; i < hi; i += NW * 32) p.dist[i] = (uint32_t)(__ldcg(p.ds + i) >> 32);
+}
+
 template <int MODE, int NW>
 __device__ __forceinline__ void worker_loop(const Params &p, CtaShared &cs, WarpStage *stages, Prefetch *pfs) {
   WarpStage &stage = stages[threadIdx.x >> 5];
@@ -514,7 +522,13 @@ __device__ __forceinline__ void worker_loop(const Params &p, CtaShared &cs, Warp
   for (;;) {
     const Interval iv = cs.iv;
     const int32_t id = cs.id;
-    if (iv.done || id >= iv.M) return;  // finished, or left through offer_kill
+    if (iv.done) {
+      // SSSP's result: the active CTAs copy the distances out of the packed words, CTA
+      // `id` of M taking the id-th stripe
+      if (MODE == MODE_SSSP && id < iv.M) copy_dist<NW>(p, id, iv.M);
+      return;
+    }
+    if (id >= iv.M) return;  // left through offer_kill
     if (MODE != MODE_BARRIER) expand<MODE, NW>(p, iv, id, stage, pf);
     if (!resizing_barrier<MODE, NW>(p, cs)) return;
   }
@@ -592,10 +606,7 @@ __device__ __forceinline__ void init_body(const Params &p, size_t tid, size_t nt
     for (size_t i = tid; i < V; i += nth) p.level[i] = -1;
     for (size_t i = tid; i < (V + 31) / 32; i += nth) p.visited[i] = 0u;
   } else if (MODE == MODE_SSSP) {
-    for (size_t i = tid; i < V; i += nth) {
-      p.dist[i] = 0xFFFFFFFFu;
-      p.stamp[i] = 0u;
-    }
+    for (size_t i = tid; i < V; i += nth) p.ds[i] = 0xFFFFFFFF00000000ull;  // unreached, never queued
   }
   // zero the control block except its header line, which thread 0 writes
   uint32_t *cw = reinterpret_cast<uint32_t *>(p.ctl);
@@ -670,7 +681,8 @@ struct coop_ctx {
   Ctl *ctl = nullptr;
   void *scratch = nullptr;
   int64_t cap_V = 0, cap_chunks = 0;
-  uint32_t *visited = nullptr, *stamp = nullptr;
+  uint32_t *visited = nullptr;
+  unsigned long long *ds = nullptr;
   uint32_t *qx[2] = {nullptr, nullptr};
   uint32_t *qv[2] = {nullptr, nullptr}, *qs[2] = {nullptr, nullptr}, *qo[2] = {nullptr, nullptr};
   std::mutex mu;         // host bookkeeping (kill/fork counters, run state)
@@ -742,7 +754,7 @@ coop_status ensure_scratch(coop_ctx *c, int64_t V, int64_t E) {
   const size_t words = (size_t)(cap + 31) / 32;
   const size_t qbytes = (size_t)cap * 4;
   const size_t xbytes = (size_t)capx * 4;
-  const size_t total = words * 4 + qbytes * 7 + xbytes * 2 + 10 * 256;
+  const size_t total = words * 4 + qbytes * 8 + xbytes * 2 + 10 * 256;
   char *base = nullptr;
   if (cudaMalloc(&base, total) != cudaSuccess) {
     (void)cudaGetLastError();
@@ -755,7 +767,7 @@ coop_status ensure_scratch(coop_ctx *c, int64_t V, int64_t E) {
     return reinterpret_cast<uint32_t *>(p);
   };
   c->visited = take(words * 4);
-  c->stamp = take(qbytes);
+  c->ds = reinterpret_cast<unsigned long long *>(take(qbytes * 2));
   for (int i = 0; i < 2; ++i) {
     c->qv[i] = take(qbytes);
     c->qs[i] = take(qbytes);
@@ -823,7 +835,7 @@ coop_status launch_run(coop_ctx *c, const coop_csr *g, const uint32_t *w, int32_
     p.level = level;
     p.dist = dist;
     p.visited = c->visited;
-    p.stamp = c->stamp;
+    p.ds = c->ds;
     for (int i = 0; i < 2; ++i) {
       p.qv[i] = c->qv[i];
       p.qs[i] = c->qs[i];
@@ -1342,7 +1354,7 @@ coop_status coop_batch_create(coop_ctx *c, const coop_job *jobs, int n, coop_bat
   for (int i = 0; i < n; ++i) {
     const size_t V = (size_t)jobs[i].graph.num_vertices, X = (size_t)(jobs[i].graph.num_edges / kIndexEdges + 2);
     const size_t need = al(sizeof(Ctl)) + al(sizeof(Mailbox)) +
-                        (jobs[i].kind == COOP_JOB_SSSP ? al(V * 4) : al((V + 31) / 32 * 4)) + 6 * al(V * 4) +
+                        (jobs[i].kind == COOP_JOB_SSSP ? al(V * 8) : al((V + 31) / 32 * 4)) + 6 * al(V * 4) +
                         2 * al(X * 4);
     off[i + 1] = off[i] + need;
     b->max_V = std::max<int64_t>(b->max_V, (int64_t)V);
@@ -1374,7 +1386,7 @@ coop_status coop_batch_create(coop_ctx *c, const coop_job *jobs, int n, coop_bat
     p = Params{};
     p.ctl = reinterpret_cast<Ctl *>(take(sizeof(Ctl)));
     p.mbox = reinterpret_cast<Mailbox *>(take(sizeof(Mailbox)));
-    if (j.kind == COOP_JOB_SSSP) p.stamp = reinterpret_cast<uint32_t *>(take(V * 4));
+    if (j.kind == COOP_JOB_SSSP) p.ds = reinterpret_cast<unsigned long long *>(take(V * 8));
     else p.visited = reinterpret_cast<uint32_t *>(take((V + 31) / 32 * 4));
     for (int q = 0; q < 2; ++q) {
       p.qv[q] = reinterpret_cast<uint32_t *>(take(V * 4));

@@ -146,7 +146,10 @@ struct Params {
   int32_t *level;
   uint32_t *dist;
   uint32_t *visited;  // BFS: 1 bit per vertex
-  uint32_t *stamp;    // SSSP: frontier round each vertex was last queued for
+  // SSSP: per vertex (tentative distance << 32) | stamp, the stamp being the frontier
+  // round the vertex was last queued for; the distances are copied out to `dist` when
+  // the traversal ends
+  unsigned long long *ds;
   uint32_t *qv[2];    // frontier queues: vertex id (SSSP)
   uint32_t *qs[2];    //                  first column index (row_off[v])
   uint32_t *qo[2];    //                  exclusive prefix of out-degrees (edge space)
@@ -581,8 +584,7 @@ __device__ __forceinline__ void master_enter(const Params &p, CtaShared &cs) {
         p.level[s] = 0;
         atomicOr(p.visited + (s >> 5), 1u << (s & 31));
       } else {
-        p.dist[s] = 0u;
-        p.stamp[s] = 1u;
+        p.ds[s] = 1ull;  // distance 0, queued for round 1
       }
       c->reached = 1ull;
       c->reached_edges = (unsigned long long)(re - rs);
