@@ -265,6 +265,7 @@ __device__ __forceinline__ void expand_range(const Params &p, const Interval &iv
   const uint32_t next_level = (uint32_t)iv.level + 1u;
   const uint32_t V = (uint32_t)p.V;
   const uint32_t E1 = c1;
+  const bool pre = iv.precheck != 0u;
 
   Window w;
   load_entry<MODE>(p, qo, qs, qv, F, Etot, wb + lane, w);
@@ -294,40 +295,72 @@ __device__ __forceinline__ void expand_range(const Params &p, const Interval &iv
     }
 
     if (MODE == MODE_BFS) {
-      uint32_t word[kUnroll];
+      if (pre) {
+        uint32_t word[kUnroll];
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        if (val[u] && vv[u] >= V) {
-          bad = true;
-          val[u] = false;
+        for (int u = 0; u < kUnroll; ++u) {
+          if (val[u] && vv[u] >= V) {
+            bad = true;
+            val[u] = false;
+          }
+          word[u] = val[u] ? *(p.visited + (vv[u] >> 5)) : 0xFFFFFFFFu;
         }
-        word[u] = val[u] ? *(p.visited + (vv[u] >> 5)) : 0xFFFFFFFFu;
-      }
-      // Row bounds of every candidate the bitmap word shows unvisited are read before
-      // its atomicOr, not after, so the two round trips overlap; a candidate that then
-      // loses the claim race wasted two cached loads.
-      int32_t ra[kUnroll], rb[kUnroll];
+        // Row bounds of every candidate the bitmap word shows unvisited are read before
+        // its atomicOr, not after, so the two round trips overlap; a candidate that then
+        // loses the claim race wasted two cached loads.
+        int32_t ra[kUnroll], rb[kUnroll];
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        const bool cand = val[u] && (word[u] & (1u << (vv[u] & 31u))) == 0u;
-        ra[u] = cand ? __ldg(p.row_off + vv[u]) : 0;
-        rb[u] = cand ? __ldg(p.row_off + vv[u] + 1) : 0;
-      }
-#pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        const uint32_t m = 1u << (vv[u] & 31u);
-        bool claim = false;
-        if (val[u] && (word[u] & m) == 0u) claim = (atomicOr(p.visited + (vv[u] >> 5), m) & m) == 0u;
-        uint32_t rs = 0u, deg = 0u;
-        bool push = false;
-        if (claim) {
-          p.level[vv[u]] = (int32_t)next_level;
-          if (ra[u] < 0 || rb[u] < ra[u] || (uint32_t)rb[u] > p.E) bad = true;
-          else { rs = (uint32_t)ra[u]; deg = (uint32_t)(rb[u] - ra[u]); push = deg > 0u; }
-          nreach += 1u;
-          ereach += deg;
+        for (int u = 0; u < kUnroll; ++u) {
+          const bool cand = val[u] && (word[u] & (1u << (vv[u] & 31u))) == 0u;
+          ra[u] = cand ? __ldg(p.row_off + vv[u]) : 0;
+          rb[u] = cand ? __ldg(p.row_off + vv[u] + 1) : 0;
         }
-        stage_push<MODE>(p, out, stage, staged, push, vv[u], rs, deg, lane);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const uint32_t m = 1u << (vv[u] & 31u);
+          bool claim = false;
+          if (val[u] && (word[u] & m) == 0u) claim = (atomicOr(p.visited + (vv[u] >> 5), m) & m) == 0u;
+          uint32_t rs = 0u, deg = 0u;
+          bool push = false;
+          if (claim) {
+            p.level[vv[u]] = (int32_t)next_level;
+            if (ra[u] < 0 || rb[u] < ra[u] || (uint32_t)rb[u] > p.E) bad = true;
+            else {
+              rs = (uint32_t)ra[u];
+              deg = (uint32_t)(rb[u] - ra[u]);
+              push = deg > 0u;
+            }
+            nreach += 1u;
+            ereach += deg;
+          }
+          stage_push<MODE>(p, out, stage, staged, push, vv[u], rs, deg, lane);
+        }
+      } else {
+        // no pre-check: every target goes straight to its atomicOr, and only the claimed
+        // ones read their row bounds
+        bool claim[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          if (val[u] && vv[u] >= V) {
+            bad = true;
+            val[u] = false;
+          }
+          const uint32_t m = 1u << (vv[u] & 31u);
+          claim[u] = val[u] && (atomicOr(p.visited + (vv[u] >> 5), m) & m) == 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          uint32_t rs = 0u, deg = 0u;
+          bool push = false;
+          if (claim[u]) {
+            p.level[vv[u]] = (int32_t)next_level;
+            if (row_of(p, vv[u], rs, deg)) push = deg > 0u;
+            else bad = true;
+            nreach += 1u;
+            ereach += deg;
+          }
+          stage_push<MODE>(p, out, stage, staged, push, vv[u], rs, deg, lane);
+        }
       }
     } else {
       // Relaxation on the packed word ds[v] = (dist << 32) | stamp.  One 64-bit atomicMin
@@ -353,7 +386,8 @@ __device__ __forceinline__ void expand_range(const Params &p, const Interval &iv
           bad = true;
           val[u] = false;
         }
-        dv[u] = val[u] ? (uint32_t)(*(volatile const unsigned long long *)(p.ds + vv[u]) >> 32) : 0u;
+        dv[u] = !val[u] ? 0u : pre ? (uint32_t)(*(volatile const unsigned long long *)(p.ds + vv[u]) >> 32)
+                                   : 0xFFFFFFFFu;
       }
       const uint32_t tag = next_level + 1u;  // stamp of "queued for the next round"
       bool imp[kUnroll];
@@ -767,13 +801,13 @@ coop_status ensure_scratch(coop_ctx *c, int64_t V, int64_t E) {
     return reinterpret_cast<uint32_t *>(p);
   };
   c->visited = take(words * 4);
-  c->ds = reinterpret_cast<unsigned long long *>(take(qbytes * 2));
   for (int i = 0; i < 2; ++i) {
     c->qv[i] = take(qbytes);
     c->qs[i] = take(qbytes);
     c->qo[i] = take(qbytes);
     c->qx[i] = take(xbytes);
   }
+  c->ds = reinterpret_cast<unsigned long long *>(take(qbytes * 2));
   c->scratch = base;
   c->cap_V = cap;
   c->cap_chunks = capx;

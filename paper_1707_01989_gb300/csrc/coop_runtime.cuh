@@ -47,6 +47,11 @@ constexpr int kCorunnerSmem = 116 * 1024;   // dynamic smem of a co-runner CTA
 constexpr uint64_t kEntryGatherNs = 20000;  // master waits this long for its launch to register
 constexpr uint32_t kIndexEdges = 128;       // granularity of the chunk index (edges per unit)
 constexpr uint32_t kChunkUnitsMax = 16;     // a work chunk spans 1..16 32-edge units, sized to the frontier
+// A claim reads the target's state (visited bit, distance) before its atomic on frontiers
+// of at least kPrecheckEdges edges, where the read saves most atomics (claim atomics in
+// bulk are far slower than loads).  On smaller frontiers the read is one more dependent
+// round trip on the level's critical path, and the claim goes straight to the atomic.
+constexpr uint32_t kPrecheckEdges = 65536;
 
 enum Mode : int { MODE_BFS = 0, MODE_SSSP = 1, MODE_BARRIER = 2 };
 
@@ -67,6 +72,7 @@ struct Interval {
   uint32_t done;   // 1: the traversal is over, every CTA leaves
   uint32_t epoch;  // epoch number that opened this interval
   uint32_t doom;   // CTAs of the previous interval with logical id >= doom leave (host kills)
+  uint32_t precheck;  // 1: read a target's state before its claim atomic (kPrecheckEdges)
 };
 
 // One barrier record (the run's trace): barrier index, microseconds since the run
@@ -357,6 +363,8 @@ __device__ __forceinline__ bool wait_epoch_at_least(const Params &p, uint32_t e)
 template <int MODE, int NW>
 __device__ void spawn_forks(const Params &p, uint32_t n);
 
+__device__ __forceinline__ uint32_t precheck_hint(uint32_t edges) { return edges >= kPrecheckEdges ? 1u : 0u; }
+
 // Releaser-private books of one release, stored after the epoch word is released: no
 // waiter reads them, and this thread's next arrival (a release) orders them before the
 // next releaser's loads.
@@ -454,6 +462,7 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
   c->host_decided = decided + (uint32_t)Wmid;
   nxt.M = Mn;
   nxt.doom = (uint32_t)Mmid;
+  nxt.precheck = precheck_hint(edges);
   c->iv = nxt;
   if (nxt.done) st_relaxed(&c->done, 1u);
 
@@ -618,6 +627,7 @@ __device__ __forceinline__ void master_enter(const Params &p, CtaShared &cs) {
   iv.done = (count == 0u || ld_relaxed(&c->err) != 0u) ? 1u : 0u;
   iv.epoch = 1u;
   iv.doom = (uint32_t)(1 + k);
+  iv.precheck = precheck_hint(edges);
   c->admitted = (uint32_t)k;
   c->t_start = gtime();
   st_relaxed(&c->launched_total, p.coop ? p.launched : gridDim.x);
