@@ -62,7 +62,10 @@ __device__ __forceinline__ void load_entry(const Params &p, const uint32_t *qo, 
     w.end = (i + 1u < F) ? qo[i + 1u] : Etot;
     if (MODE == MODE_SSSP) {
       w.u = qv[i];
-      w.du = (uint32_t)(*(volatile const unsigned long long *)(p.ds + w.u) >> 32);
+      // a weak (L1-cacheable) read: after the barrier's acquire it returns the distance
+      // at the barrier or a later, lower one, and a lowering after the barrier queues
+      // the vertex again for the next round
+      w.du = (uint32_t)(p.ds[w.u] >> 32);
     }
   } else {
     w.off = 0xFFFFFFFFu;
@@ -168,13 +171,27 @@ constexpr int kUnroll = 4;  // 32-edge groups a warp handles per iteration
 // other, so the DRAM latency of the column stream overlaps the L2 round trips of the
 // claim.  Every lane copies and later reads only its own words of a slot.
 constexpr int kStages = 2;  // landing slots: copies run kStages - 1 iterations ahead
-struct Prefetch {
+template <int MODE>
+struct Landing {  // BFS (and the barrier self-test): columns only
+  uint32_t col[kStages][kUnroll][32];
+};
+template <>
+struct Landing<MODE_SSSP> {
   uint32_t col[kStages][kUnroll][32];
   uint32_t w[kStages][kUnroll][32];
   uint32_t du[kStages][kUnroll][32];
 };
-static_assert(kDefaultWorkerWarps * (sizeof(WarpStage) + sizeof(Prefetch)) <= (size_t)kReserveSmem,
-              "per-warp staging must fit in a traversal CTA's dynamic shared memory");
+
+// Dynamic shared memory of a traversal CTA: NW enqueue stages, then NW landing buffers,
+// and at least kTraverseSmemMin (SM exclusivity).  The batch kernel runs both kinds of
+// job and takes the SSSP size.
+__host__ __device__ constexpr int traverse_smem(int mode, int nw) {
+  const size_t need =
+      (size_t)nw * (sizeof(WarpStage) + (mode == MODE_SSSP ? sizeof(Landing<MODE_SSSP>) : sizeof(Landing<MODE_BFS>)));
+  const int rounded = (int)((need + 1023) / 1024 * 1024);
+  return rounded > kTraverseSmemMin ? rounded : kTraverseSmemMin;
+}
+static_assert(traverse_smem(MODE_SSSP, kDefaultWorkerWarps) <= 227 * 1024, "traversal CTA shared memory");
 
 __device__ __forceinline__ void cp_async4(void *sdst, const void *gsrc) {
   const uint32_t sa = (uint32_t)__cvta_generic_to_shared(sdst);
@@ -216,7 +233,7 @@ __device__ __forceinline__ bool slide(const Params &p, const uint32_t *qo, const
 template <int MODE>
 __device__ __forceinline__ void issue_groups(const Params &p, const uint32_t *qo, const uint32_t *qs,
                                              const uint32_t *qv, uint32_t F, uint32_t Etot, uint32_t c,
-                                             uint32_t E1, Window &w, uint32_t &wb, Prefetch &pf, int sb,
+                                             uint32_t E1, Window &w, uint32_t &wb, Landing<MODE> &pf, int sb,
                                              unsigned lane, unsigned lm_le) {
 #pragma unroll
   for (int u = 0; u < kUnroll; ++u) {
@@ -237,7 +254,7 @@ __device__ __forceinline__ void issue_groups(const Params &p, const uint32_t *qo
     if (e < E1) {
       const uint32_t pos = s0 + (e - o0);
       cp_async4(&pf.col[sb][u][lane], p.col + pos);
-      if (MODE == MODE_SSSP) {
+      if constexpr (MODE == MODE_SSSP) {
         cp_async4(&pf.w[sb][u][lane], p.w + pos);
         pf.du[sb][u][lane] = du;
       }
@@ -252,7 +269,7 @@ __device__ __forceinline__ void issue_groups(const Params &p, const uint32_t *qo
 // the next kUnroll column loads in flight while it works on the current ones.
 template <int MODE>
 __device__ __forceinline__ void expand_range(const Params &p, const Interval &iv, uint32_t c0, uint32_t c1,
-                                             uint32_t wb, WarpStage &stage, Prefetch &pf, uint32_t &staged,
+                                             uint32_t wb, WarpStage &stage, Landing<MODE> &pf, uint32_t &staged,
                                              bool &bad, bool &ovf, uint32_t &nreach, uint64_t &ereach) {
   const unsigned lane = threadIdx.x & 31u;
   const uint32_t Etot = iv.edges;
@@ -294,7 +311,7 @@ __device__ __forceinline__ void expand_range(const Params &p, const Interval &iv
       vv[u] = val[u] ? pf.col[sb][u][lane] : 0xFFFFFFFFu;
     }
 
-    if (MODE == MODE_BFS) {
+    if constexpr (MODE != MODE_SSSP) {
       if (pre) {
         uint32_t word[kUnroll];
 #pragma unroll
@@ -386,8 +403,7 @@ __device__ __forceinline__ void expand_range(const Params &p, const Interval &iv
           bad = true;
           val[u] = false;
         }
-        dv[u] = !val[u] ? 0u : pre ? (uint32_t)(*(volatile const unsigned long long *)(p.ds + vv[u]) >> 32)
-                                   : 0xFFFFFFFFu;
+        dv[u] = !val[u] ? 0u : pre ? (uint32_t)(p.ds[vv[u]] >> 32) : 0xFFFFFFFFu;
       }
       const uint32_t tag = next_level + 1u;  // stamp of "queued for the next round"
       bool imp[kUnroll];
@@ -435,7 +451,7 @@ __device__ __forceinline__ void expand_range(const Params &p, const Interval &iv
 // over the rest.  The enqueue built a chunk index (entry holding each unit's first
 // edge), so a chunk starts without any search.
 template <int MODE, int NW>
-__device__ void expand(const Params &p, const Interval &iv, int32_t id, WarpStage &stage, Prefetch &pf) {
+__device__ void expand(const Params &p, const Interval &iv, int32_t id, WarpStage &stage, Landing<MODE> &pf) {
   const unsigned lane = threadIdx.x & 31u;
   const uint32_t Etot = iv.edges;
   const uint32_t GW = (uint32_t)iv.M * NW;
@@ -489,7 +505,7 @@ namespace coopdev {
 // at the next resizing barrier; the parent grid completes only after they have left.
 template <int MODE, int NW>
 __device__ void spawn_forks(const Params &p, uint32_t n) {
-  coop_traverse<MODE, NW><<<n, (NW + 1) * 32, kReserveSmem, cudaStreamFireAndForget>>>(p, 1);
+  coop_traverse<MODE, NW><<<n, (NW + 1) * 32, traverse_smem(MODE, NW), cudaStreamFireAndForget>>>(p, 1);
 }
 }  // namespace coopdev
 
@@ -550,9 +566,9 @@ __device__ __forceinline__ void copy_dist(const Params &p, int32_t id, int32_t M
 }
 
 template <int MODE, int NW>
-__device__ __forceinline__ void worker_loop(const Params &p, CtaShared &cs, WarpStage *stages, Prefetch *pfs) {
+__device__ __forceinline__ void worker_loop(const Params &p, CtaShared &cs, WarpStage *stages, Landing<MODE> *pfs) {
   WarpStage &stage = stages[threadIdx.x >> 5];
-  Prefetch &pf = pfs[threadIdx.x >> 5];
+  Landing<MODE> &pf = pfs[threadIdx.x >> 5];
   for (;;) {
     const Interval iv = cs.iv;
     const int32_t id = cs.id;
@@ -563,7 +579,7 @@ __device__ __forceinline__ void worker_loop(const Params &p, CtaShared &cs, Warp
       return;
     }
     if (id >= iv.M) return;  // left through offer_kill
-    if (MODE != MODE_BARRIER) expand<MODE, NW>(p, iv, id, stage, pf);
+    if constexpr (MODE != MODE_BARRIER) expand<MODE, NW>(p, iv, id, stage, pf);
     if (!resizing_barrier<MODE, NW>(p, cs)) return;
   }
 }
@@ -594,7 +610,7 @@ __device__ __forceinline__ void traverse_body(const Params &p, bool master, CtaS
   }
   // dynamic shared memory: NW enqueue stages, then NW landing buffers
   worker_loop<MODE, NW>(p, cs, reinterpret_cast<WarpStage *>(dyn),
-                        reinterpret_cast<Prefetch *>(dyn + NW * sizeof(WarpStage)));
+                        reinterpret_cast<Landing<MODE> *>(dyn + NW * sizeof(WarpStage)));
   if (threadIdx.x == 0) *(volatile int32_t *)&cs.workers_left = 1;
 }
 
@@ -760,6 +776,17 @@ struct DeviceGuard {
 inline uint32_t load_acquire(const uint32_t *p) { return __atomic_load_n(p, __ATOMIC_ACQUIRE); }
 inline void store_release(uint32_t *p, uint32_t v) { __atomic_store_n(p, v, __ATOMIC_RELEASE); }
 
+// A traversal kernel's dynamic shared memory, and the carveout hint that leaves the rest
+// of the SM's L1/shared storage to L1 (the driver takes the smallest carveout that holds
+// the CTA's shared memory).
+bool set_traverse_attrs(const void *k, int smem) {
+  return !cuda_failed(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+                      "set traversal smem") &&
+         !cuda_failed(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                           (int)cudaSharedmemCarveoutMaxL1),
+                      "set traversal carveout");
+}
+
 bool running(coop_ctx *c) { return c->launched && cudaEventQuery(c->ev_done) == cudaErrorNotReady; }
 
 // Fold the CTAs the device has surrendered into the host's books (always), and once no
@@ -835,9 +862,9 @@ const void *traverse_fn(int nw) {
 template <int MODE>
 void launch_traverse(int nw, int grid, const Params &p, int join, cudaStream_t s) {
   switch (nw) {
-    case 31: coop_traverse<MODE, 31><<<grid, 32 * 32, kReserveSmem, s>>>(p, join); break;
-    case 23: coop_traverse<MODE, 23><<<grid, 24 * 32, kReserveSmem, s>>>(p, join); break;
-    default: coop_traverse<MODE, 15><<<grid, 16 * 32, kReserveSmem, s>>>(p, join); break;
+    case 31: coop_traverse<MODE, 31><<<grid, 32 * 32, traverse_smem(MODE, 31), s>>>(p, join); break;
+    case 23: coop_traverse<MODE, 23><<<grid, 24 * 32, traverse_smem(MODE, 23), s>>>(p, join); break;
+    default: coop_traverse<MODE, 15><<<grid, 16 * 32, traverse_smem(MODE, 15), s>>>(p, join); break;
   }
 }
 
@@ -965,13 +992,13 @@ coop_status coop_init(int device, int max_ctas, int threads_per_cta, coop_ctx **
     return fail(COOP_ECUDA);
   c->nw = nw;
   const void *kernels[] = {traverse_fn<MODE_BFS>(nw), traverse_fn<MODE_SSSP>(nw), traverse_fn<MODE_BARRIER>(nw)};
+  const int modes[] = {MODE_BFS, MODE_SSSP, MODE_BARRIER};
   int per_sm = 1 << 30;
-  for (const void *k : kernels) {
-    if (cuda_failed(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kReserveSmem),
-                    "set traversal smem"))
-      return fail(COOP_ECUDA);
+  for (int i = 0; i < 3; ++i) {
+    const int smem = traverse_smem(modes[i], nw);
+    if (!set_traverse_attrs(kernels[i], smem)) return fail(COOP_ECUDA);
     int nb = 0;
-    if (cuda_failed(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, (nw + 1) * 32, kReserveSmem), "occupancy"))
+    if (cuda_failed(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernels[i], (nw + 1) * 32, smem), "occupancy"))
       return fail(COOP_ECUDA);
     per_sm = std::min(per_sm, nb);
   }
@@ -1349,9 +1376,15 @@ void batch_enqueue(coop_batch *b, cudaStream_t s) {
   const dim3 ig((unsigned)std::max<int64_t>(1, std::min<int64_t>((b->max_V + 511) / 512, 64)), (unsigned)b->n);
   coop_init_batch_kernel<<<ig, 512, 0, s>>>(b->d_params);
   switch (c->nw) {
-    case 31: coop_traverse_batch<31><<<b->total, 32 * 32, kReserveSmem, s>>>(b->d_params, b->d_first, b->n); break;
-    case 23: coop_traverse_batch<23><<<b->total, 24 * 32, kReserveSmem, s>>>(b->d_params, b->d_first, b->n); break;
-    default: coop_traverse_batch<15><<<b->total, 16 * 32, kReserveSmem, s>>>(b->d_params, b->d_first, b->n); break;
+    case 31:
+      coop_traverse_batch<31><<<b->total, 32 * 32, traverse_smem(MODE_SSSP, 31), s>>>(b->d_params, b->d_first, b->n);
+      break;
+    case 23:
+      coop_traverse_batch<23><<<b->total, 24 * 32, traverse_smem(MODE_SSSP, 23), s>>>(b->d_params, b->d_first, b->n);
+      break;
+    default:
+      coop_traverse_batch<15><<<b->total, 16 * 32, traverse_smem(MODE_SSSP, 15), s>>>(b->d_params, b->d_first, b->n);
+      break;
   }
 }
 
@@ -1403,9 +1436,7 @@ coop_status coop_batch_create(coop_ctx *c, const coop_job *jobs, int n, coop_bat
       cuda_failed(cudaMalloc((void **)&b->d_params, sizeof(Params) * n), "batch table") ||
       cuda_failed(cudaMalloc((void **)&b->d_first, sizeof(uint32_t) * n), "batch table"))
     return fail(COOP_ENOMEM);
-  if (cuda_failed(cudaFuncSetAttribute(batch_fn(c->nw), cudaFuncAttributeMaxDynamicSharedMemorySize, kReserveSmem),
-                  "set batch smem"))
-    return fail(COOP_ECUDA);
+  if (!set_traverse_attrs(batch_fn(c->nw), traverse_smem(MODE_SSSP, c->nw))) return fail(COOP_ECUDA);
   b->params.resize(n);
   for (int i = 0; i < n; ++i) {
     const coop_job &j = jobs[i];
@@ -1986,13 +2017,11 @@ extern "C" coop_status coop_bfs_noalloc(const coop_csr *g, int32_t source, int32
     void *ptr = nullptr;
     if (cuda_failed(cudaGetSymbolAddress(&ptr, g_noalloc_scratch), "scratch symbol address")) return COOP_ECUDA;
     const void *k = traverse_fn<MODE_BFS>(kDefaultWorkerWarps);
-    if (cuda_failed(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kReserveSmem),
-                    "set traversal smem"))
-      return COOP_ECUDA;
+    if (!set_traverse_attrs(k, traverse_smem(MODE_BFS, kDefaultWorkerWarps))) return COOP_ECUDA;
     int nb = 0, sms = 0;
     if (cuda_failed(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "sm count") ||
         cuda_failed(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, (kDefaultWorkerWarps + 1) * 32,
-                                                                  kReserveSmem),
+                                                                  traverse_smem(MODE_BFS, kDefaultWorkerWarps)),
                     "occupancy"))
       return COOP_ECUDA;
     if (nb < 1) {

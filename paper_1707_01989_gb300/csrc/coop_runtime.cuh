@@ -40,10 +40,14 @@ namespace coopdev {
 constexpr int kDefaultWorkerWarps = 31;
 constexpr int kMaxCtas = 2048;              // admission slot table; N <= kMaxCtas
 constexpr int kLogCap = 4096;               // resize-log records per run
-// A traversal CTA and a co-runner CTA each take more than half of an SM's 228 KB of
-// shared memory, so neither can share an SM with the other (or with its own kind).
-constexpr int kReserveSmem = 120 * 1024;    // dynamic smem of a traversal CTA (staging + landing buffers)
-constexpr int kCorunnerSmem = 116 * 1024;   // dynamic smem of a co-runner CTA
+// SM exclusivity by shared memory: a traversal CTA takes at least kTraverseSmemMin of an
+// SM's 228 KB and a co-runner CTA kCorunnerSmem, more than the SM holds together, so a
+// co-runner only ever starts on an SM that no traversal CTA occupies.  A traversal CTA
+// asks for no more than its staging needs, so that the rest of the SM's 256 KB of
+// L1/shared storage serves as L1 (the BFS visited bitmap is read through L1).
+constexpr int kTraverseSmemMin = 56 * 1024;
+constexpr int kCorunnerSmem = 176 * 1024;
+static_assert(kTraverseSmemMin + kCorunnerSmem + 2 * 1024 > 228 * 1024, "co-runner must not fit beside a traversal CTA");
 constexpr uint64_t kEntryGatherNs = 20000;  // master waits this long for its launch to register
 constexpr uint32_t kIndexEdges = 128;       // granularity of the chunk index (edges per unit)
 constexpr uint32_t kChunkUnitsMax = 16;     // a work chunk spans 1..16 32-edge units, sized to the frontier
