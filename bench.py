@@ -184,6 +184,23 @@ def config_of(name, g, extra=None):
     return c
 
 
+def job_time(t_local: float, world: int, device) -> float:
+    """Seconds of the whole job: the slowest rank's time (MAX all-reduce, then a barrier)."""
+    if world <= 1:
+        return t_local
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t_local], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(tt.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, t_job: float) -> float:
+    """G-units per second of the whole job: every rank processes its own replica."""
+    return units_per_rank * world / t_job / 1e9
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle on the same workload (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -292,13 +309,8 @@ def main():
             step_ms.append(e0.elapsed_time(e1))
             kern_us.append(coop.coop_get_stats(ctx).kernel_us)
     torch.cuda.synchronize(dev)
-    t_step = statistics.mean(step_ms) / 1e3
-    if world > 1:
-        tt = torch.tensor([t_step], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
-        dist.barrier()
-    value = es * world / t_step / 1e9
+    t_step = job_time(statistics.mean(step_ms) / 1e3, world, dev)
+    value = whole_job_rate(es, world, t_step)
 
     # roofline of the dominant kernel (the persistent traversal kernel)
     hbm, peak_kind = peaks()
@@ -332,7 +344,7 @@ def main():
         e1.synchronize()
         if i >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
-    e2e_val = es * world / (statistics.mean(e2e_ms) / 1e3) / 1e9
+    e2e_val = whole_job_rate(es, world, job_time(statistics.mean(e2e_ms) / 1e3, world, dev))
 
     if rank == 0:
         extras = {}
