@@ -480,6 +480,92 @@ def corunner(coop, ctx, dev, csr, src, lv, stream, period_s=1.0 / 60.0, duration
             "coop_slowdown": round(per_co / per_alone, 4)}
 
 
+def preemption(coop, ctx, dev, stream, period_s=1.0 / 60.0, duration_s=1.0):
+    """Co-runner latency with and without cooperation, on back-to-back 256x256 grid BFS
+    traversals (about 3 ms each, 511 resizing barriers).
+
+    Without cooperation (the non-cooperative baseline kernel, the co-runner only on a
+    high-priority stream) the co-runner's CTAs start when a traversal ends and frees its
+    SMs: CTAs are not preempted.  With cooperation the co-runner asks for half the CTAs
+    (coop_request_resources), the traversal gives them up at its next kill point, and
+    the co-runner runs beside it.  Latency = host time from the co-runner's request (or
+    launch) to its completion; solo = the same with no traversal in flight."""
+    import numpy as np
+    import torch
+    import graphgen as gg
+    g = gg.grid(256, 256)
+    ro = torch.from_numpy(np.array(g.row_off)).to(dev)
+    col = torch.from_numpy(np.array(g.col)).to(dev)
+    lv = torch.empty(g.num_vertices, dtype=torch.int32, device=dev)
+    csr = coop.make_csr(ro, col)
+    N = coop.coop_query(ctx)["max_ctas"]
+    half = N // 2
+    n_el = 16 * 1024 * 1024
+    x = torch.rand(n_el, device=dev)
+    y = torch.rand(n_el, device=dev)
+    cs = torch.cuda.Stream(device=dev, priority=-1)
+    for _ in range(3):
+        coop.coop_saxpy(half, 2.0, x, y, stream=cs)
+    cs.synchronize()
+
+    def plain_job():
+        t0 = time.perf_counter()
+        coop.coop_saxpy(half, 2.0, x, y, stream=cs)
+        cs.synchronize()
+        return (time.perf_counter() - t0) * 1e3
+
+    def coop_job():
+        t0 = time.perf_counter()
+        got = coop.coop_request_resources(ctx, half, timeout_us=2_000_000)
+        coop.coop_saxpy(half, 2.0, x, y, stream=cs)
+        cs.synchronize()
+        t1 = time.perf_counter()
+        coop.coop_release(ctx, got)
+        return (t1 - t0) * 1e3
+
+    def run(traverse, job):
+        lat = []
+        stop = threading.Event()
+
+        def ticker():
+            nxt = time.perf_counter()
+            while not stop.is_set():
+                lat.append(job())
+                nxt += period_s
+                time.sleep(max(0.0, nxt - time.perf_counter()))
+
+        traverse()
+        stream.synchronize()
+        th = threading.Thread(target=ticker)
+        t0 = time.perf_counter()
+        th.start()
+        n = 0
+        while time.perf_counter() - t0 < duration_s:
+            traverse()
+            n += 1
+        stream.synchronize()
+        per = (time.perf_counter() - t0) / n
+        stop.set()
+        th.join()
+        return lat, per
+
+    def pct(v, q):
+        v = sorted(v)
+        return round(v[min(len(v) - 1, int(round(q * (len(v) - 1))))], 4)
+
+    solo = [plain_job() for _ in range(30)]
+    lat_plain, per_plain = run(lambda: coop.coop_bfs_baseline(ctx, csr, 0, lv, stream=stream), plain_job)
+    lat_coop, per_coop = run(lambda: coop.coop_bfs(ctx, csr, 0, lv, stream=stream), coop_job)
+    coop.coop_sync(ctx)
+    return {"graph": "grid 256x256 BFS, back to back", "period_ms": round(period_s * 1e3, 2), "claimed_ctas": half,
+            "solo_ms_p50": pct(solo, 0.5), "solo_ms_p99": pct(solo, 0.99),
+            "no_coop": {"jobs": len(lat_plain), "latency_ms_p50": pct(lat_plain, 0.5),
+                        "latency_ms_p99": pct(lat_plain, 0.99), "traversal_ms": round(per_plain * 1e3, 4)},
+            "coop": {"jobs": len(lat_coop), "latency_ms_p50": pct(lat_coop, 0.5),
+                     "latency_ms_p99": pct(lat_coop, 0.99), "traversal_ms": round(per_coop * 1e3, 4)},
+            "p99_no_coop_vs_coop": round(pct(lat_plain, 0.99) / pct(lat_coop, 0.99), 3)}
+
+
 def batched(coop, ctx, dev, stream, flush, n_inst=64, seed=3, steps=5):
     """Batched form: 64 independent R-MAT instances (scales uniform in 12..20, edge factor
     16), a BFS and an SSSP job each, run as one autotuned, CUDA-graph-captured launch,
@@ -680,7 +766,8 @@ def serving(coop, dev, n_graphs=32, rate=200.0, duration_s=3.0, slots=4, budget=
 
 
 def secondary(coop, ctx, dev, stream, flush, args):
-    """BFS on R-MAT 22, grid BFS, barrier latency and the non-cooperative baseline ratio."""
+    """BFS on R-MAT 22, grid BFS, the co-runner with and without cooperation, batching,
+    serving, barrier latency and the non-cooperative baseline ratio."""
     import numpy as np
     import torch
     import graphgen as gg
@@ -740,14 +827,31 @@ def secondary(coop, ctx, dev, stream, flush, args):
     ok = bool(np.array_equal(lv.cpu().numpy(), np.add(*np.divmod(np.arange(65536), 256))))
     out["grid_bfs"] = {"levels": 511, "ms": round(ms, 4), "kernel_us": round(kus, 2),
                        "us_per_level": round(kus / 511, 3), "closed_form_ok": ok}
+    out["preemption"] = preemption(coop, ctx, dev, stream)
+    del ro, col, lv
     out["batched"] = batched(coop, ctx, dev, stream, flush)
     out["serving"] = serving(coop, dev)
-    # empty resizing barriers at M = N
+    # empty resizing barriers: at M = N, at M = N/2 (half the CTAs lent), and at M = N
+    # with a forced schedule that kills or forks at about one barrier in eight
     n = 20000
+    N = coop.coop_query(ctx)["max_ctas"]
     f = lambda: coop.coop_barrier_bench(ctx, n, stream=stream, stats=False)
-    f()
-    ms, kus = timed(f, 3)
-    out["barrier_us"] = round(kus / n, 4)
+
+    def per_barrier():
+        f()
+        _, kus = timed(f, 3)
+        return round(kus / n, 4)
+
+    out["barrier_us"] = per_barrier()
+    got = coop.coop_request_resources(ctx, N // 2)
+    out["barrier_us_half"] = per_barrier()
+    coop.coop_release(ctx, got)
+    coop.coop_set_schedule(ctx, 7, p_kill=1.0 / 16, p_fork=1.0 / 16)
+    us = per_barrier()
+    st = coop.coop_get_stats(ctx)
+    coop.coop_set_schedule(ctx, 0, 0.0, 0.0)
+    out["barrier_us_resizing"] = {"us": us, "kills": st.kills, "forks": st.forks, "barriers": st.barriers,
+                                  "min_active": st.min_active}
     return out
 
 

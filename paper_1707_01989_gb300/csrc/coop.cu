@@ -267,10 +267,18 @@ __device__ __forceinline__ void issue_groups(const Params &p, const uint32_t *qo
 // edge c0.  Software-pipelined over iterations of kUnroll 32-edge groups: the copies of
 // iteration i+1 are started, then iteration i's targets are claimed, so every lane keeps
 // the next kUnroll column loads in flight while it works on the current ones.
+//
+// Returns the warp's next chunk (nchunks: none).  With `more`, lane 0 claims it from the
+// cursor at the start of the range's last iteration, so the atomic's latency overlaps
+// that iteration's work.  This is also the offer_kill point of the expansion: a CTA inside
+// the host's kill target claims nothing more (the other CTAs take the rest of the level)
+// and leaves at the barrier, at most one iteration after the check.
 template <int MODE>
-__device__ __forceinline__ void expand_range(const Params &p, const Interval &iv, uint32_t c0, uint32_t c1,
-                                             uint32_t wb, WarpStage &stage, Landing<MODE> &pf, uint32_t &staged,
-                                             bool &bad, bool &ovf, uint32_t &nreach, uint64_t &ereach) {
+__device__ __forceinline__ uint32_t expand_range(const Params &p, const Interval &iv, uint32_t c0, uint32_t c1,
+                                                 uint32_t wb, WarpStage &stage, Landing<MODE> &pf,
+                                                 uint32_t &staged, bool &bad, bool &ovf, uint32_t &nreach,
+                                                 uint64_t &ereach, bool more, int32_t id, uint32_t GW,
+                                                 uint32_t nchunks) {
   const unsigned lane = threadIdx.x & 31u;
   const uint32_t Etot = iv.edges;
   const uint32_t F = iv.count;
@@ -299,7 +307,11 @@ __device__ __forceinline__ void expand_range(const Params &p, const Interval &iv
     else cp_async_commit();
   }
   int sb = 0, sn = kStages - 1;
+  uint32_t jn = nchunks;
   for (uint32_t c = c0; c < E1; c += 32u * kUnroll, ci += 32u * kUnroll) {
+    if (more && lane == 0 && c + 32u * kUnroll >= E1 &&
+        !(p.coop && doomed(ld_relaxed64(&p.ctl->kill_target), iv.epoch, id)))
+      jn = GW + atomicAdd(&p.ctl->cursor.v, 1u);
     if (ci < E1) issue_groups<MODE>(p, qo, qs, qv, F, Etot, ci, E1, w, wb, pf, sn, lane, lm_le);
     else cp_async_commit();
     cp_async_wait<kStages - 1>();  // this iteration's slot has landed; later ones stay in flight
@@ -441,6 +453,7 @@ __device__ __forceinline__ void expand_range(const Params &p, const Interval &iv
     sb = sb + 1 == kStages ? 0 : sb + 1;
     sn = sn + 1 == kStages ? 0 : sn + 1;
   }
+  return __shfl_sync(kFull, jn, 0);
 }
 
 // Expand this warp's part of the interval.  The edge space is cut into chunks of
@@ -466,19 +479,12 @@ __device__ void expand(const Params &p, const Interval &iv, int32_t id, WarpStag
   uint32_t staged = 0u, nreach = 0u;
   uint64_t ereach = 0ull;
   bool bad = false, ovf = false;
+  const bool more = GW < nchunks;  // chunks beyond the first M * NW are claimed from the cursor
   while (j < nchunks) {
-    // claim the next chunk now; the atomic's latency overlaps this chunk's work
-    uint32_t jn = nchunks;
-    if (lane == 0 && GW < nchunks) {
-      // offer_kill point: a CTA inside the host's kill target stops claiming chunks (it
-      // finishes the chunk in hand; the others take the rest) and leaves at the barrier
-      if (!(p.coop && doomed(ld_relaxed64(&p.ctl->kill_target), iv.epoch, id)))
-        jn = GW + atomicAdd(&p.ctl->cursor.v, 1u);
-    }
     const uint32_t c0 = j * csize;
     const uint32_t c1 = min(c0 + csize, Etot);
-    expand_range<MODE>(p, iv, c0, c1, qx[c0 / kIndexEdges], stage, pf, staged, bad, ovf, nreach, ereach);
-    j = __shfl_sync(kFull, jn, 0);
+    j = expand_range<MODE>(p, iv, c0, c1, qx[c0 / kIndexEdges], stage, pf, staged, bad, ovf, nreach, ereach,
+                           more, id, GW, nchunks);
   }
   if (staged) stage_flush<MODE>(p, out, stage, staged, lane);
   // this warp's newly reached vertices and their out-edges (the TEPS numerator)
@@ -521,24 +527,28 @@ __device__ __forceinline__ void scheduler_warp(const Params &p, const volatile i
   Ctl *c = p.ctl;
   uint32_t forks_seen = p.fork_base, freed_seen = 0u;
   for (;;) {
-    const uint32_t r = ld_sys(&p.mbox->kill_req);
-    // a consistent (epoch, interval, decided) snapshot: epoch read before and after
-    const uint32_t e = ld_acquire(&c->epoch.v);
-    const uint32_t decided = ld_relaxed(&c->host_decided);
-    const Interval iv = read_iv(c);
-    const int32_t pend = (int32_t)(r - p.kill_base - decided);
-    if (pend > 0 && iv.epoch == e && !iv.done && ld_acquire(&c->epoch.v) == e) {
-      const int32_t T = max(1, iv.M - pend);
-      unsigned long long kt = ld_relaxed64(&c->kill_target);
-      for (;;) {
-        const uint32_t ke = (uint32_t)(kt >> 32);
-        if ((int32_t)(ke - e) > 0) break;  // the word already belongs to a later interval
-        const bool same = ke == e;
-        if (same && ((kt & kTargetClosed) || (int32_t)(kt & 0x7FFFFFFFull) <= T)) break;
-        const unsigned long long nv = ((unsigned long long)e << 32) | (unsigned long long)(uint32_t)T;
-        const unsigned long long prev = atomicCAS(&c->kill_target, kt, nv);
-        if (prev == kt) break;
-        kt = prev;
+    // both host counters in one system-scope load: (fork_req << 32) | kill_req
+    const uint64_t req = ld_sys64(&p.mbox->kill_req);
+    const uint32_t r = (uint32_t)req, f = (uint32_t)(req >> 32);
+    if ((int32_t)(r - p.kill_base - ld_relaxed(&c->host_decided)) > 0) {
+      // a consistent (epoch, interval, decided) snapshot: epoch read before and after
+      const uint32_t e = ld_acquire(&c->epoch.v);
+      const uint32_t decided = ld_relaxed(&c->host_decided);
+      const Interval iv = read_iv(c);
+      const int32_t pend = (int32_t)(r - p.kill_base - decided);
+      if (pend > 0 && iv.epoch == e && !iv.done && ld_acquire(&c->epoch.v) == e) {
+        const int32_t T = max(1, iv.M - pend);
+        unsigned long long kt = ld_relaxed64(&c->kill_target);
+        for (;;) {
+          const uint32_t ke = (uint32_t)(kt >> 32);
+          if ((int32_t)(ke - e) > 0) break;  // the word already belongs to a later interval
+          const bool same = ke == e;
+          if (same && ((kt & kTargetClosed) || (int32_t)(kt & 0x7FFFFFFFull) <= T)) break;
+          const unsigned long long nv = ((unsigned long long)e << 32) | (unsigned long long)(uint32_t)T;
+          const unsigned long long prev = atomicCAS(&c->kill_target, kt, nv);
+          if (prev == kt) break;
+          kt = prev;
+        }
       }
     }
     const uint32_t sur = ld_relaxed(&c->surrendered);
@@ -546,7 +556,6 @@ __device__ __forceinline__ void scheduler_warp(const Params &p, const volatile i
       st_sys(&p.mbox->freed, p.kill_base + sur);
       freed_seen = sur;
     }
-    const uint32_t f = ld_sys(&p.mbox->fork_req);
     if ((int32_t)(f - forks_seen) > 0) {
       const uint32_t n = f - forks_seen;
       forks_seen = f;
@@ -554,7 +563,7 @@ __device__ __forceinline__ void scheduler_warp(const Params &p, const volatile i
       spawn_forks<MODE, NW>(p, n);
     }
     if (ld_relaxed(&c->done) != 0u || ld_relaxed(&c->err) != 0u || *workers_left != 0) return;
-    __nanosleep(500);
+    __nanosleep(200);
   }
 }
 
@@ -686,6 +695,12 @@ __global__ void __launch_bounds__(512) coop_init_batch_kernel(const Params *__re
   uint32_t *mw = reinterpret_cast<uint32_t *>(p.mbox);
   for (size_t i = tid; i < sizeof(Mailbox) / 4; i += nth) mw[i] = 0u;
 }
+
+// Device-side launch warm-up: the first launch from the device in a process sets up the
+// device runtime's launch path, which must not happen inside the scheduler warp of a
+// running traversal (it would hold up the host's next request).
+__global__ void coop_warm_child() {}
+__global__ void coop_warm_parent() { coop_warm_child<<<1, 32, 0, cudaStreamFireAndForget>>>(); }
 
 // The co-running task: y = a*x + y, grid-stride, vectorised where aligned.
 __global__ void __launch_bounds__(1024) coop_saxpy_kernel(int64_t n, float a, const float *__restrict__ x,
@@ -1023,6 +1038,13 @@ coop_status coop_init(int device, int max_ctas, int threads_per_cta, coop_ctx **
     }
     coop_saxpy_kernel<<<1, 1024, kCorunnerSmem>>>(0, 0.f, nullptr, nullptr);  // n = 0: no work
     if (cuda_failed(cudaGetLastError(), "co-runner warm-up")) return fail(COOP_ECUDA);
+    cudaStream_t ws = nullptr;
+    if (cuda_failed(cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking), "warm-up stream")) return fail(COOP_ECUDA);
+    coop_warm_parent<<<1, 1, 0, ws>>>();
+    const bool warm_ok = !cuda_failed(cudaGetLastError(), "device launch warm-up") &&
+                         !cuda_failed(cudaStreamSynchronize(ws), "device launch warm-up");
+    cudaStreamDestroy(ws);
+    if (!warm_ok) return fail(COOP_ECUDA);
   }
   const int cap = std::min(per_sm * c->sm_count, kMaxCtas);
   c->N = max_ctas == 0 ? cap : std::min(max_ctas, cap);

@@ -134,6 +134,7 @@ struct Ctl {
 
 // Host <-> device mailbox in mapped pinned host memory.
 struct alignas(128) Mailbox {
+  // kill_req and fork_req share one 8-byte word, read by the device in one load
   uint32_t kill_req;  // host -> device: cumulative CTAs requested by the scheduler
   uint32_t fork_req;  // host -> device: cumulative CTAs the scheduler gave back
   uint32_t pad0[30];
@@ -238,6 +239,11 @@ __device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t *p, uint32_t v) {
 __device__ __forceinline__ uint32_t ld_sys(const uint32_t *p) {
   uint32_t v;
   asm volatile("ld.relaxed.sys.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint64_t ld_sys64(const void *p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.sys.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 __device__ __forceinline__ void st_sys(uint32_t *p, uint32_t v) {

@@ -211,3 +211,16 @@ def test_saxpy_ragged(ctx):
         coop.coop_saxpy(7, 3.0, x, y)
         torch.cuda.synchronize()
         torch.testing.assert_close(y, ref)
+
+
+def test_barrier_bench_under_forced_schedule(ctx):
+    """Empty resizing barriers with a kill or fork at about one barrier in eight: every
+    barrier completes, and the resizes form a legal Fork/Kill sequence (Appendix A)."""
+    coop.coop_set_schedule(ctx, 7, p_kill=1.0 / 16, p_fork=1.0 / 16)
+    st = coop.coop_barrier_bench(ctx, 3000)
+    coop.coop_set_schedule(ctx, 0, 0.0, 0.0)
+    assert st.status == coop.COOP_OK and st.barriers == 3000
+    assert st.kills > 0 and st.forks > 0
+    _replay(ctx, st)
+    st = coop.coop_barrier_bench(ctx, 100)
+    assert st.kills == 0 and st.forks == 0  # the schedule is off again
