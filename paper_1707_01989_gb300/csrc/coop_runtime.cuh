@@ -474,7 +474,7 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
   nxt.doom = (uint32_t)Mmid;
   nxt.precheck = precheck_hint(edges);
   c->iv = nxt;
-  if (nxt.done) st_relaxed(&c->done, 1u);
+  if (nxt.done) st_release(&c->done, 1u);  // after the admission slots (join_enter relies on it)
 
   bk.admitted = A + (uint32_t)k;
   bk.barriers = barriers;
@@ -560,10 +560,20 @@ __device__ __forceinline__ bool join_enter(const Params &p, CtaShared &cs) {
   const uint32_t t = atomicAdd(&c->join_ticket.v, 1u);
   const uint64_t t0 = gtime();
   uint64_t s = 0;
+  auto admitted = [&](uint64_t v) { return v != 0ull && (uint32_t)(v & 0x7FFFFull) == (t & 0x7FFFFu); };
   for (uint32_t spin = 0;; ++spin) {
     s = ld_acquire64(&c->slot[t % kMaxCtas]);
-    if (s != 0ull && (uint32_t)(s & 0x7FFFFull) == (t & 0x7FFFFu)) break;
-    if (ld_relaxed(&c->done) != 0u || ld_relaxed(&c->err) != 0u || ld_relaxed(&c->run) != p.run) return false;
+    if (admitted(s)) break;
+    if (ld_acquire(&c->done) != 0u) {
+      // The run is over -- possibly already at the master's entry, with this CTA among
+      // the admitted.  The slots are written before `done` is released, so a second look
+      // at the slot is conclusive: an admitted CTA goes on (it copies its share of the
+      // result), any other leaves.
+      s = ld_acquire64(&c->slot[t % kMaxCtas]);
+      if (admitted(s)) break;
+      return false;
+    }
+    if (ld_relaxed(&c->err) != 0u || ld_relaxed(&c->run) != p.run) return false;
     // a CTA that is never admitted simply leaves after the limit; it holds nobody up
     if ((spin & 15u) == 15u && gtime() - t0 > 4ull * p.timeout_ns) return false;
     __nanosleep(100);
@@ -648,7 +658,7 @@ __device__ __forceinline__ void master_enter(const Params &p, CtaShared &cs) {
   c->frontier_total = count;
   c->iv = iv;
   if (iv.done) {
-    st_relaxed(&c->done, 1u);
+    st_release(&c->done, 1u);  // after the admission slots (join_enter relies on it)
     const uint32_t e = ld_relaxed(&c->err);
     publish_stats(p, (int)e);
   }

@@ -117,6 +117,25 @@ def test_baselines_match(ctx):
     assert_same(d, oracle.dijkstra(g, w, src), "baseline sssp")
 
 
+def test_sssp_over_at_entry_writes_every_distance(ctx):
+    """A source without out-edges ends the traversal at the master's entry.  Every CTA
+    admitted there still copies its stripe of the distances out: the output is pre-filled
+    with garbage, and the run is repeated, since a CTA that took the end of the run for a
+    refusal of its admission would leave its stripe unwritten only now and then."""
+    g = gg.rmat(16, 16, seed=5)
+    src = int(np.flatnonzero(np.diff(np.array(g.row_off)) == 0)[0])
+    w = gg.weights(g, 6)
+    dg = DevGraph(g, w)
+    exp = oracle.dijkstra(g, w, src)
+    assert (exp != 0xFFFFFFFF).sum() == 1
+    for i in range(50):
+        out = dg.empty()
+        out.fill_(0x5A5A5A5A)
+        f = coop.coop_sssp_baseline if i % 5 == 4 else coop.coop_sssp
+        f(ctx, dg.csr, dg.w, src, out, stats=True)
+        assert_same(out.cpu().numpy().view(np.uint32), exp, f"source without out-edges, run {i}")
+
+
 def test_repeated_runs_reuse_scratch(ctx):
     big = gg.rmat(16, 16, seed=21)
     small = gg.grid(40, 30)
