@@ -566,6 +566,64 @@ def preemption(coop, ctx, dev, stream, period_s=1.0 / 60.0, duration_s=1.0):
             "p99_no_coop_vs_coop": round(pct(lat_plain, 0.99) / pct(lat_coop, 0.99), 3)}
 
 
+def gather_by_kill_mode(coop, ctx, dev, stream, period_s=0.005, duration_s=0.6):
+    """Gather time -- coop_request_resources(half the CTAs) until granted -- under each
+    kill mode, on back-to-back traversals of R-MAT 22 BFS (6 wide levels) and of the
+    256x256 grid BFS (511 narrow levels): the regular versus query barrier comparison of
+    Sec. 5.4 ("Responsiveness"), plus the query barrier with kill points between chunks."""
+    import numpy as np
+    import torch
+    import graphgen as gg
+    N = coop.coop_query(ctx)["max_ctas"]
+    half = N // 2
+    modes = (("simple", coop.COOP_KILL_SIMPLE), ("query", coop.COOP_KILL_QUERY), ("chunk", coop.COOP_KILL_CHUNK))
+    out = {}
+    for gname, g, src in (("rmat22_bfs", gg.rmat(22, 16, seed=22), None), ("grid256_bfs", gg.grid(256, 256), 0)):
+        src = gg.max_out_degree_vertex(g) if src is None else src
+        ro = torch.from_numpy(np.array(g.row_off)).to(dev)
+        col = torch.from_numpy(np.array(g.col)).to(dev)
+        lv = torch.empty(g.num_vertices, dtype=torch.int32, device=dev)
+        csr = coop.make_csr(ro, col)
+        res = {}
+        for mname, m in modes:
+            coop.coop_set_kill_mode(ctx, m)
+            gat = []
+            stop = threading.Event()
+
+            def ticker():
+                nxt = time.perf_counter()
+                while not stop.is_set():
+                    t0 = time.perf_counter()
+                    got = coop.coop_request_resources(ctx, half, timeout_us=2_000_000)
+                    gat.append((time.perf_counter() - t0) * 1e3)
+                    coop.coop_release(ctx, got)
+                    nxt += period_s
+                    time.sleep(max(0.0, nxt - time.perf_counter()))
+
+            coop.coop_bfs(ctx, csr, src, lv, stream=stream)
+            stream.synchronize()
+            th = threading.Thread(target=ticker)
+            t0 = time.perf_counter()
+            th.start()
+            n = 0
+            while time.perf_counter() - t0 < duration_s:
+                coop.coop_bfs(ctx, csr, src, lv, stream=stream)
+                n += 1
+            stream.synchronize()
+            stop.set()
+            th.join()
+            coop.coop_sync(ctx)
+            g_ms = sorted(gat)
+            q = lambda f: round(g_ms[min(len(g_ms) - 1, int(round(f * (len(g_ms) - 1))))], 4)
+            res[mname] = {"requests": len(g_ms), "gather_ms_p50": q(0.5), "gather_ms_p99": q(0.99),
+                          "gather_ms_max": round(g_ms[-1], 4), "traversal_ms": round(duration_s / n * 1e3, 4)}
+        coop.coop_set_kill_mode(ctx, coop.COOP_KILL_CHUNK)
+        out[gname] = res
+        del ro, col, lv
+    out["claimed_ctas"] = half
+    return out
+
+
 def batched(coop, ctx, dev, stream, flush, n_inst=64, seed=3, steps=5):
     """Batched form: 64 independent R-MAT instances (scales uniform in 12..20, edge factor
     16), a BFS and an SSSP job each, run as one autotuned, CUDA-graph-captured launch,
@@ -828,6 +886,7 @@ def secondary(coop, ctx, dev, stream, flush, args):
     out["grid_bfs"] = {"levels": 511, "ms": round(ms, 4), "kernel_us": round(kus, 2),
                        "us_per_level": round(kus / 511, 3), "closed_form_ok": ok}
     out["preemption"] = preemption(coop, ctx, dev, stream)
+    out["gather_by_kill_mode"] = gather_by_kill_mode(coop, ctx, dev, stream)
     del ro, col, lv
     out["batched"] = batched(coop, ctx, dev, stream, flush)
     out["serving"] = serving(coop, dev)

@@ -165,6 +165,22 @@ coop_status coop_set_schedule(coop_ctx *ctx, uint64_t seed, double p_kill, doubl
 coop_status coop_set_timeout(coop_ctx *ctx, int64_t timeout_us);
 
 /*
+ * Where the context's traversals serve coop_request_resources (Sec. 4.2, "An Efficient
+ * Resizing Barrier"); takes effect at the next launch.
+ *   COOP_KILL_CHUNK   (default) the query barrier -- the releaser fixes W, the CTAs with
+ *                     the W largest ids leave, and a CTA that sees the request while
+ *                     waiting leaves at once -- plus a kill point between two chunks of
+ *                     an interval, so a request is served within one chunk of work.
+ *   COOP_KILL_QUERY   the query barrier alone: requests are served at resizing barriers.
+ *   COOP_KILL_SIMPLE  the regular barrier: every CTA offers to leave once, on arriving at
+ *                     a barrier, and only the CTA with the largest live id may, so the
+ *                     order of arrival decides how many leave per barrier.
+ * The results do not depend on the mode; COOP_EINVAL for an unknown mode.
+ */
+enum { COOP_KILL_CHUNK = 0, COOP_KILL_QUERY = 1, COOP_KILL_SIMPLE = 2 };
+coop_status coop_set_kill_mode(coop_ctx *ctx, int mode);
+
+/*
  * Kernel timing: when on, every traversal records CUDA events around its persistent
  * kernel on the launch stream and coop_stats.kernel_us reports the elapsed time.
  */

@@ -20,7 +20,8 @@ from . import _build
 __all__ = [
     "CoopError", "CoopUnavailable", "Stats", "CSR", "coop_init", "coop_destroy", "coop_bfs", "coop_sssp",
     "coop_request_resources", "coop_release", "coop_sync", "coop_get_stats", "coop_get_resize_log",
-    "coop_set_schedule", "coop_set_timeout", "coop_set_timing", "coop_query", "coop_bfs_baseline", "coop_sssp_baseline",
+    "coop_set_schedule", "coop_set_timeout", "coop_set_timing", "coop_set_kill_mode", "COOP_KILL_CHUNK",
+    "COOP_KILL_QUERY", "COOP_KILL_SIMPLE", "coop_query", "coop_bfs_baseline", "coop_sssp_baseline",
     "coop_barrier_bench", "coop_saxpy", "coop_bfs_noalloc", "coop_status_string", "Job", "Batch", "make_job",
     "coop_batch_create", "coop_batch_set_ctas", "coop_batch_tune", "coop_batch_run", "coop_batch_get_stats",
     "coop_batch_destroy", "coop_last_cuda_error", "library_path", "load_library", "Server", "QueryResult",
@@ -118,6 +119,7 @@ def load_library():
                 "coop_set_schedule": [vp, u64, ctypes.c_double, ctypes.c_double],
                 "coop_set_timeout": [vp, i64],
                 "coop_set_timing": [vp, ctypes.c_int],
+                "coop_set_kill_mode": [vp, ctypes.c_int],
                 "coop_query": [vp, ip, ip, ip, ip],
                 "coop_barrier_bench": [vp, i32, i32, vp, sp],
                 "coop_saxpy": [ctypes.c_int, i64, ctypes.c_float, vp, vp, vp],
@@ -328,6 +330,13 @@ def coop_set_schedule(ctx, seed: int, p_kill: float, p_fork: float) -> None:
 
 def coop_set_timeout(ctx, timeout_us: int) -> None:
     _check(load_library().coop_set_timeout(_h(ctx), int(timeout_us)), "coop_set_timeout")
+
+
+COOP_KILL_CHUNK, COOP_KILL_QUERY, COOP_KILL_SIMPLE = 0, 1, 2
+
+
+def coop_set_kill_mode(ctx, mode: int) -> None:
+    _check(load_library().coop_set_kill_mode(_h(ctx), int(mode)), "coop_set_kill_mode")
 
 
 def coop_set_timing(ctx, on: bool = True) -> None:

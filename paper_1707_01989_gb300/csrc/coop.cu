@@ -310,7 +310,7 @@ __device__ __forceinline__ uint32_t expand_range(const Params &p, const Interval
   uint32_t jn = nchunks;
   for (uint32_t c = c0; c < E1; c += 32u * kUnroll, ci += 32u * kUnroll) {
     if (more && lane == 0 && c + 32u * kUnroll >= E1 &&
-        !(p.coop && doomed(ld_relaxed64(&p.ctl->kill_target), iv.epoch, id)))
+        !(p.coop && p.kill_mode == KILL_CHUNK && doomed(ld_relaxed64(&p.ctl->kill_target), iv.epoch, id)))
       jn = GW + atomicAdd(&p.ctl->cursor.v, 1u);
     if (ci < E1) issue_groups<MODE>(p, qo, qs, qv, F, Etot, ci, E1, w, wb, pf, sn, lane, lm_le);
     else cp_async_commit();
@@ -525,12 +525,18 @@ namespace {
 template <int MODE, int NW>
 __device__ __forceinline__ void scheduler_warp(const Params &p, const volatile int32_t *workers_left) {
   Ctl *c = p.ctl;
-  uint32_t forks_seen = p.fork_base, freed_seen = 0u;
+  uint32_t forks_seen = p.fork_base, freed_seen = 0u, host_req_seen = 0u;
   for (;;) {
     // both host counters in one system-scope load: (fork_req << 32) | kill_req
     const uint64_t req = ld_sys64(&p.mbox->kill_req);
     const uint32_t r = (uint32_t)req, f = (uint32_t)(req >> 32);
-    if ((int32_t)(r - p.kill_base - ld_relaxed(&c->host_decided)) > 0) {
+    if (p.kill_mode == KILL_SIMPLE) {
+      // the regular barrier: arriving CTAs compare this with the kills already decided
+      if (r - p.kill_base != host_req_seen) {
+        host_req_seen = r - p.kill_base;
+        st_relaxed(&c->host_req, host_req_seen);
+      }
+    } else if ((int32_t)(r - p.kill_base - ld_relaxed(&c->host_decided)) > 0) {
       // a consistent (epoch, interval, decided) snapshot: epoch read before and after
       const uint32_t e = ld_acquire(&c->epoch.v);
       const uint32_t decided = ld_relaxed(&c->host_decided);
@@ -741,6 +747,7 @@ struct coop_ctx {
   cudaEvent_t ev_done = nullptr;
   cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;  // kernel timing (optional)
   bool timing = false;
+  uint32_t kill_mode = 0;  // KILL_CHUNK
   Mailbox *mbox = nullptr;    // host view
   Mailbox *mbox_d = nullptr;  // device view of the same pinned page
   Ctl *ctl = nullptr;
@@ -934,6 +941,7 @@ coop_status launch_run(coop_ctx *c, const coop_csr *g, const uint32_t *w, int32_
     p.n_barriers = n_barriers;
     p.extra_wait = (uint32_t)std::max(0, extra_wait);
     p.coop = coop ? 1u : 0u;
+    p.kill_mode = c->kill_mode;
     p.mode = MODE;
 
     c->mbox->err = 0;
@@ -1266,6 +1274,13 @@ coop_status coop_set_timeout(coop_ctx *c, int64_t timeout_us) {
   if (!c || timeout_us < 1) return COOP_EINVAL;
   std::lock_guard<std::mutex> lk(c->mu);
   c->timeout_us = timeout_us;
+  return COOP_OK;
+}
+
+coop_status coop_set_kill_mode(coop_ctx *c, int mode) {
+  if (!c || mode < COOP_KILL_CHUNK || mode > COOP_KILL_SIMPLE) return COOP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->kill_mode = (uint32_t)mode;
   return COOP_OK;
 }
 

@@ -59,6 +59,15 @@ constexpr uint32_t kPrecheckEdges = 65536;
 
 enum Mode : int { MODE_BFS = 0, MODE_SSSP = 1, MODE_BARRIER = 2 };
 
+// Where the host's requests for CTAs are served (Sec. 4.2, "An Efficient Resizing Barrier"):
+//  KILL_CHUNK   the query barrier, plus a kill point between two chunks of an interval
+//  KILL_QUERY   the query barrier alone: the scheduler's W is fixed at a release, and the
+//               CTAs with the W largest ids leave at the barrier
+//  KILL_SIMPLE  the regular barrier: each CTA offers to leave once, on arrival, and only
+//               the CTA with the largest live id can, so arrival order decides how many
+//               leave per barrier
+enum KillMode : uint32_t { KILL_CHUNK = 0, KILL_QUERY = 1, KILL_SIMPLE = 2 };
+
 enum Err : int {
   ERR_TIMEOUT = -4,   // COOP_ETIMEOUT
   ERR_OVERFLOW = -6,  // COOP_EOVERFLOW
@@ -105,9 +114,13 @@ struct Ctl {
   // host kill target of the running interval: (epoch << 32) | closed << 31 | T, where
   // CTAs with logical id >= T leave; lowered by the scheduler warp, closed by the releaser
   alignas(128) unsigned long long kill_target;
-  uint32_t surrendered;   // CTAs that left on a host kill target
-  uint32_t host_decided;  // host kills fixed at closed targets (releaser)
-  uint32_t pad_k[28];
+  uint32_t surrendered;   // CTAs that left on a host request
+  uint32_t host_decided;  // host kills fixed at releases (releaser)
+  uint32_t host_req;      // KILL_SIMPLE: the host's requests of this run (scheduler warp)
+  uint32_t pad_k0;
+  // KILL_SIMPLE: (live CTAs << 32) | CTAs that left at this barrier's offer_kill
+  unsigned long long live;
+  uint32_t pad_k[24];
   // header line: written once per run by the init kernel, then by error/done paths
   alignas(128) uint32_t run;
   uint32_t unused_h;
@@ -183,6 +196,7 @@ struct Params {
   int32_t n_barriers;  // MODE_BARRIER: intervals to run
   uint32_t extra_wait; // barrier self-test: arrivals that never come
   uint32_t coop;       // 0: non-cooperative baseline (fixed ids, no scheduler)
+  uint32_t kill_mode;  // where host requests are served: KILL_CHUNK, KILL_QUERY or KILL_SIMPLE
   int32_t mode;        // MODE_BFS / MODE_SSSP (read by the batch kernel)
 };
 
@@ -399,10 +413,13 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
   // release can no longer land on this epoch; a lower open target is then put back.
   // Issued first so that its round trip overlaps the loads below.
   unsigned long long closed = 0ull, kt = 0ull;
-  if (p.coop) {
+  const bool simple = p.kill_mode == KILL_SIMPLE;
+  if (p.coop && !simple) {
     closed = ((unsigned long long)cur.epoch << 32) | kTargetClosed;
     kt = atomicExch(&c->kill_target, closed | (unsigned long long)(uint32_t)M);
   }
+  // regular barrier: the CTAs that left at their offer_kill on arrival (largest ids first)
+  const unsigned long long live = simple ? ld_relaxed64(&c->live) : 0ull;
   // Everything else the release needs, in one batch of independent loads: the output
   // queue's counters and the releaser-private books.
   const uint32_t out = cur.sel ^ 1u;
@@ -417,8 +434,12 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
   const uint32_t R = p.coop ? ld_relaxed(&c->join_ticket.v) : 0u;
   const uint64_t now = gtime();
   int32_t Mmid = M;
-  if (p.coop && (uint32_t)(kt >> 32) == cur.epoch) Mmid = min(M, max(1, (int32_t)(kt & 0x7FFFFFFFull)));
-  if (Mmid < M) st_relaxed64(&c->kill_target, closed | (unsigned long long)(uint32_t)Mmid);
+  if (simple) {
+    Mmid = (int32_t)(live >> 32);
+  } else {
+    if (p.coop && (uint32_t)(kt >> 32) == cur.epoch) Mmid = min(M, max(1, (int32_t)(kt & 0x7FFFFFFFull)));
+    if (Mmid < M) st_relaxed64(&c->kill_target, closed | (unsigned long long)(uint32_t)Mmid);
+  }
 
   Interval nxt = cur;
   nxt.epoch = cur.epoch + 1u;
@@ -472,6 +493,7 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
   c->host_decided = decided + (uint32_t)Wmid;
   nxt.M = Mn;
   nxt.doom = (uint32_t)Mmid;
+  if (simple) st_relaxed64(&c->live, (unsigned long long)(uint32_t)Mn << 32);
   nxt.precheck = precheck_hint(edges);
   c->iv = nxt;
   if (nxt.done) st_release(&c->done, 1u);  // after the admission slots (join_enter relies on it)
@@ -526,6 +548,23 @@ __device__ __forceinline__ bool resizing_barrier(const Params &p, CtaShared &cs)
     // while waiting (it has arrived, and the target is only ever lowered until the
     // releaser stamps it closed, so the closed target includes it)
     bool leave = false;
+    if (p.coop && p.kill_mode == KILL_SIMPLE && cs.id > 0) {
+      // the regular barrier's offer_kill, once, on arrival: leave if the host still
+      // wants CTAs and this CTA has the largest live id
+      const uint32_t want = ld_relaxed(&c->host_req) - ld_relaxed(&c->host_decided);
+      unsigned long long lv = ld_relaxed64(&c->live);
+      for (;;) {
+        const uint32_t ml = (uint32_t)(lv >> 32), kd = (uint32_t)lv;
+        if (kd >= want || (uint32_t)cs.id + 1u != ml) break;
+        const unsigned long long prev =
+            atomicCAS(&c->live, lv, ((unsigned long long)(ml - 1u) << 32) | (unsigned long long)(kd + 1u));
+        if (prev == lv) {
+          leave = true;
+          break;
+        }
+        lv = prev;
+      }
+    }
     const uint32_t old = atom_add_acq_rel(&c->arrive.v, 1u);
     bool ok = true;
     if (old == (uint32_t)(cur.M - 1) + p.extra_wait) {
@@ -535,8 +574,8 @@ __device__ __forceinline__ bool resizing_barrier(const Params &p, CtaShared &cs)
       st_release(&c->epoch.v, cur.epoch + 1u);
       release_books(p, bk);
       cs.iv = nxt;
-    } else {
-      const int w = wait_release(p, cur.epoch, p.coop ? cs.id : -1);
+    } else if (!leave) {
+      const int w = wait_release(p, cur.epoch, (p.coop && p.kill_mode != KILL_SIMPLE) ? cs.id : -1);
       ok = w != 0;
       if (w == 1) cs.iv = read_iv(c);
       if (w == 2) leave = true;
@@ -649,6 +688,7 @@ __device__ __forceinline__ void master_enter(const Params &p, CtaShared &cs) {
   iv.doom = (uint32_t)(1 + k);
   iv.precheck = precheck_hint(edges);
   c->admitted = (uint32_t)k;
+  c->live = (unsigned long long)(uint32_t)iv.M << 32;
   c->t_start = gtime();
   st_relaxed(&c->launched_total, p.coop ? p.launched : gridDim.x);
   c->initial_active = iv.M;

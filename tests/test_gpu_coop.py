@@ -224,3 +224,67 @@ def test_barrier_bench_under_forced_schedule(ctx):
     _replay(ctx, st)
     st = coop.coop_barrier_bench(ctx, 100)
     assert st.kills == 0 and st.forks == 0  # the schedule is off again
+
+
+@pytest.mark.parametrize("mode", ["chunk", "query", "simple"])
+def test_kill_modes_serve_requests(ctx, mode):
+    """Each place a host request can be served (Sec. 4.2: the regular barrier, the query
+    barrier, and the query barrier with kill points between chunks) frees the CTAs asked
+    for, logs a legal resize sequence and leaves every result unchanged."""
+    import torch
+    m = {"chunk": coop.COOP_KILL_CHUNK, "query": coop.COOP_KILL_QUERY, "simple": coop.COOP_KILL_SIMPLE}[mode]
+    coop.coop_set_kill_mode(ctx, m)
+    try:
+        N = coop.coop_query(ctx)["max_ctas"]
+        half = N // 2
+        s = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        coop.coop_barrier_bench(ctx, 400000, stream=s, stats=False)
+        time.sleep(0.02)
+        assert coop.coop_request_resources(ctx, half, timeout_us=2_000_000) == half
+        coop.coop_release(ctx, half)
+        assert coop.coop_sync(ctx) == coop.COOP_OK
+        st = coop.coop_get_stats(ctx)
+        log, _ = _replay(ctx, st)
+        kill_barriers = [r for r in coop.coop_get_resize_log(ctx) if r[4] > 0]
+        assert sum(r[4] for r in kill_barriers) >= half
+        if mode == "simple":  # one offer_kill per CTA and barrier: the kills spread over barriers
+            assert len(kill_barriers) >= 2
+        g = gg.rmat(14, 16, seed=3)
+        w = gg.weights(g, 4)
+        src = gg.max_out_degree_vertex(g)
+        dg = DevGraph(g, w)
+        exp_l, exp_d = oracle.bfs(g, src), oracle.dijkstra(g, w, src)
+        stop = threading.Event()
+        errors = []
+
+        def arbiter():
+            rng = np.random.default_rng(1)
+            try:
+                while not stop.is_set():
+                    got = coop.coop_request_resources(ctx, int(rng.integers(1, 60)), timeout_us=500_000)
+                    time.sleep(0.0003)
+                    coop.coop_release(ctx, got)
+            except Exception as exc:  # surfaced below
+                errors.append(exc)
+
+        t = threading.Thread(target=arbiter)
+        t.start()
+        try:
+            for i in range(6):
+                lv, _ = run_bfs(ctx, dg, src)
+                assert_same(lv, exp_l, f"bfs, kill mode {mode}, run {i}")
+                d, _ = run_sssp(ctx, dg, src)
+                assert_same(d, exp_d, f"sssp, kill mode {mode}, run {i}")
+        finally:
+            stop.set()
+            t.join()
+        assert not errors, errors
+        coop.coop_sync(ctx)
+    finally:
+        coop.coop_set_kill_mode(ctx, coop.COOP_KILL_CHUNK)
+
+
+def test_kill_mode_rejects_unknown(ctx):
+    with pytest.raises(coop.CoopError):
+        coop.coop_set_kill_mode(ctx, 3)
