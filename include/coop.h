@@ -116,6 +116,17 @@ coop_status coop_sssp(coop_ctx *ctx, const coop_csr *g, const uint32_t *d_weight
                       int32_t source, uint32_t *d_dist, coop_stream stream, coop_stats *stats);
 
 /*
+ * Topology-driven single-source shortest paths (Table 1 "p-sssp", read as Pannotia's
+ * formulation): every iteration scans all vertices in three resizing-barrier intervals --
+ * relax (each vertex lowered by the previous update relaxes its out-edges into a cost
+ * array), update (dist = min(dist, cost); the lowered vertices are the next relax's), and
+ * check (the run ends after an iteration that lowered nothing).  Same arguments, result
+ * and errors as coop_sssp; host requests are served at its barriers.
+ */
+coop_status coop_sssp_topo(coop_ctx *ctx, const coop_csr *g, const uint32_t *d_weights, int32_t source,
+                           uint32_t *d_dist, coop_stream stream, coop_stats *stats);
+
+/*
  * The scheduler asks the running cooperative kernel for n_ctas CTAs (Sec. 4.2,
  * "Launching Kernels and Managing Workgroups": command K_c to provide N - N_a
  * workgroups via offer_kill).  Blocks until the CTAs have left (or, with no traversal

@@ -19,6 +19,7 @@ from . import _build
 
 __all__ = [
     "CoopError", "CoopUnavailable", "Stats", "CSR", "coop_init", "coop_destroy", "coop_bfs", "coop_sssp",
+    "coop_sssp_topo",
     "coop_request_resources", "coop_release", "coop_sync", "coop_get_stats", "coop_get_resize_log",
     "coop_set_schedule", "coop_set_timeout", "coop_set_timing", "coop_set_kill_mode", "COOP_KILL_CHUNK",
     "COOP_KILL_QUERY", "COOP_KILL_SIMPLE", "coop_query", "coop_bfs_baseline", "coop_sssp_baseline",
@@ -109,6 +110,7 @@ def load_library():
                 "coop_destroy": [vp],
                 "coop_bfs": [vp, cp, i32, vp, vp, sp],
                 "coop_sssp": [vp, cp, vp, i32, vp, vp, sp],
+                "coop_sssp_topo": [vp, cp, vp, i32, vp, vp, sp],
                 "coop_bfs_baseline": [vp, cp, i32, vp, vp, sp],
                 "coop_sssp_baseline": [vp, cp, vp, i32, vp, vp, sp],
                 "coop_request_resources": [vp, ctypes.c_int, ctypes.c_int, ip],
@@ -261,6 +263,15 @@ def coop_sssp(ctx, g: CSR, weights, source: int, dist, stream=None, stats: bool 
     st = load_library().coop_sssp(_h(ctx), ctypes.byref(g), _ptr(weights, None, g.num_edges, "weights"),
                                   int(source), _ptr(dist, None, g.num_vertices, "dist"), _stream(stream), sp)
     _check(st, "coop_sssp", ok)
+    return s
+
+
+def coop_sssp_topo(ctx, g: CSR, weights, source: int, dist, stream=None, stats: bool = False, ok=(COOP_OK,)):
+    """Topology-driven SSSP (p-sssp): same result as coop_sssp."""
+    s, sp = _stats_ptr(stats)
+    st = load_library().coop_sssp_topo(_h(ctx), ctypes.byref(g), _ptr(weights, None, g.num_edges, "weights"),
+                                       int(source), _ptr(dist, None, g.num_vertices, "dist"), _stream(stream), sp)
+    _check(st, "coop_sssp_topo", ok)
     return s
 
 

@@ -573,6 +573,106 @@ __device__ __forceinline__ void scheduler_warp(const Params &p, const volatile i
   }
 }
 
+// Topology-driven SSSP, one interval of an iteration (Table 1, p-sssp: three resizing
+// barriers per iteration).  cost[] lives in the packed-word scratch, the "changed" flags
+// in the bitmap.  Work is partitioned by logical id as in Fig. 4, recomputed from the
+// current M: warp id * NW + w of stride M * NW, 32 vertices at a time.
+//   relax  (level % 3 == 0): every vertex lowered by the last update relaxes its
+//          out-edges into cost[] (atomicMin);
+//   update (level % 3 == 1): dist = min(dist, cost); the flags of the next relax are the
+//          vertices lowered now; the number lowered is counted;
+//   check  (level % 3 == 2): no work -- the releaser ends the run when the update
+//          lowered nothing.
+template <int NW>
+__device__ __forceinline__ void topo_interval(const Params &p, const Interval &iv, int32_t id) {
+  const unsigned lane = threadIdx.x & 31u;
+  const uint32_t V = (uint32_t)p.V;
+  uint32_t *cost = reinterpret_cast<uint32_t *>(p.ds);
+  const uint32_t phase = (uint32_t)iv.level % 3u;
+  if (phase == 0u) {
+    // warp-cooperative rows: warp id * NW + w takes 32 vertices at a time; for each flagged
+    // one, the 32 lanes stride over its out-edges (a thread per vertex would leave an
+    // R-MAT hub's 10^5 edges to one thread)
+    unsigned long long nrel = 0ull;
+    bool bad = false, ovf = false;
+    for (uint32_t base = ((uint32_t)id * NW + (threadIdx.x >> 5)) * 32u; base < V;
+         base += (uint32_t)iv.M * NW * 32u) {
+      unsigned m = p.visited[base >> 5];
+      if (base + 32u > V) m &= (1u << (V - base)) - 1u;
+      while (m) {
+        const uint32_t u = base + (uint32_t)(__ffs(m) - 1);
+        m &= m - 1u;
+        const uint32_t du = p.dist[u];
+        const int32_t a = __ldg(p.row_off + u), b = __ldg(p.row_off + u + 1);
+        if (a < 0 || b < a || (uint32_t)b > p.E) {
+          bad = true;
+          continue;
+        }
+        nrel += (unsigned long long)(b - a);
+        for (int32_t e0 = a; e0 < b; e0 += 64) {
+          // two edges per lane in flight
+          uint32_t v[2], wt[2];
+          bool ok[2];
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            const int32_t e = e0 + 32 * k + (int32_t)lane;
+            ok[k] = e < b;
+            v[k] = ok[k] ? (uint32_t)__ldg(p.col + e) : 0u;
+            wt[k] = ok[k] ? __ldg(p.w + e) : 0u;
+          }
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            if (!ok[k]) continue;
+            if (v[k] >= V) {
+              bad = true;
+              continue;
+            }
+            const uint64_t nd = (uint64_t)du + (uint64_t)wt[k];
+            if (nd >= 0xFFFFFFFFull) ovf = true;
+            else if ((uint32_t)nd < cost[v[k]]) atomicMin(cost + v[k], (uint32_t)nd);
+          }
+        }
+      }
+    }
+    if (lane == 0 && nrel) atomicAdd(&p.ctl->qctr[1], nrel);
+    if (__any_sync(kFull, bad) && lane == 0) raise_err(p, ERR_GRAPH);
+    if (__any_sync(kFull, ovf) && lane == 0) p.ctl->ovf = 1u;
+  } else if (phase == 1u) {
+    uint32_t lowered = 0u, nreach = 0u;
+    unsigned long long ereach = 0ull;
+    for (uint32_t base = ((uint32_t)id * NW + (threadIdx.x >> 5)) * 32u; base < V;
+         base += (uint32_t)iv.M * NW * 32u) {
+      const uint32_t v = base + lane;
+      bool low = false;
+      if (v < V) {
+        const uint32_t cv = cost[v], dv = p.dist[v];
+        if (cv < dv) {
+          p.dist[v] = cv;
+          low = true;
+          if (dv == 0xFFFFFFFFu) {  // first time reached
+            nreach += 1u;
+            ereach += (unsigned long long)(__ldg(p.row_off + v + 1) - __ldg(p.row_off + v));
+          }
+        }
+      }
+      const unsigned m = __ballot_sync(kFull, low);
+      if (lane == 0) p.visited[base >> 5] = m;  // the whole word: flags of the next relax
+      lowered += (uint32_t)__popc(m);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      nreach += __shfl_xor_sync(kFull, nreach, o);
+      ereach += __shfl_xor_sync(kFull, ereach, o);
+    }
+    if (lane == 0) {
+      if (lowered) atomicAdd(&p.ctl->qctr[0], (unsigned long long)lowered);
+      if (nreach) {
+        atomicAdd(&p.ctl->reached, (unsigned long long)nreach);
+        atomicAdd(&p.ctl->reached_edges, ereach);
+      }
+    }
+  }
+}
+
 template <int NW>
 __device__ __forceinline__ void copy_dist(const Params &p, int32_t id, int32_t M) {
   const size_t V = (size_t)p.V;
@@ -594,7 +694,8 @@ __device__ __forceinline__ void worker_loop(const Params &p, CtaShared &cs, Warp
       return;
     }
     if (id >= iv.M) return;  // left through offer_kill
-    if constexpr (MODE != MODE_BARRIER) expand<MODE, NW>(p, iv, id, stage, pf);
+    if constexpr (MODE == MODE_PSSSP) topo_interval<NW>(p, iv, id);
+    else if constexpr (MODE != MODE_BARRIER) expand<MODE, NW>(p, iv, id, stage, pf);
     if (!resizing_barrier<MODE, NW>(p, cs)) return;
   }
 }
@@ -672,6 +773,13 @@ __device__ __forceinline__ void init_body(const Params &p, size_t tid, size_t nt
     for (size_t i = tid; i < (V + 31) / 32; i += nth) p.visited[i] = 0u;
   } else if (MODE == MODE_SSSP) {
     for (size_t i = tid; i < V; i += nth) p.ds[i] = 0xFFFFFFFF00000000ull;  // unreached, never queued
+  } else if (MODE == MODE_PSSSP) {
+    uint32_t *cost = reinterpret_cast<uint32_t *>(p.ds);
+    for (size_t i = tid; i < V; i += nth) {
+      p.dist[i] = 0xFFFFFFFFu;
+      cost[i] = 0xFFFFFFFFu;
+    }
+    for (size_t i = tid; i < (V + 31) / 32; i += nth) p.visited[i] = 0u;
   }
   // zero the control block except its header line, which thread 0 writes
   uint32_t *cw = reinterpret_cast<uint32_t *>(p.ctl);
@@ -1014,10 +1122,11 @@ coop_status coop_init(int device, int max_ctas, int threads_per_cta, coop_ctx **
   if (cuda_failed(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device), "sm count"))
     return fail(COOP_ECUDA);
   c->nw = nw;
-  const void *kernels[] = {traverse_fn<MODE_BFS>(nw), traverse_fn<MODE_SSSP>(nw), traverse_fn<MODE_BARRIER>(nw)};
-  const int modes[] = {MODE_BFS, MODE_SSSP, MODE_BARRIER};
+  const void *kernels[] = {traverse_fn<MODE_BFS>(nw), traverse_fn<MODE_SSSP>(nw), traverse_fn<MODE_BARRIER>(nw),
+                           traverse_fn<MODE_PSSSP>(nw)};
+  const int modes[] = {MODE_BFS, MODE_SSSP, MODE_BARRIER, MODE_PSSSP};
   int per_sm = 1 << 30;
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < 4; ++i) {
     const int smem = traverse_smem(modes[i], nw);
     if (!set_traverse_attrs(kernels[i], smem)) return fail(COOP_ECUDA);
     int nb = 0;
@@ -1038,6 +1147,7 @@ coop_status coop_init(int device, int max_ctas, int threads_per_cta, coop_ctx **
   // while a traversal runs would not start until the traversal ended.
   {
     const void *all[] = {traverse_fn<MODE_BFS>(nw), traverse_fn<MODE_SSSP>(nw), traverse_fn<MODE_BARRIER>(nw),
+                         traverse_fn<MODE_PSSSP>(nw), (const void *)coop_init_kernel<MODE_PSSSP>,
                          (const void *)coop_init_kernel<MODE_BFS>, (const void *)coop_init_kernel<MODE_SSSP>,
                          (const void *)coop_init_kernel<MODE_BARRIER>, (const void *)coop_saxpy_kernel};
     for (const void *k : all) {
@@ -1100,6 +1210,15 @@ coop_status coop_sssp(coop_ctx *c, const coop_csr *g, const uint32_t *d_weights,
   if (st != COOP_OK) return st;
   if (g->num_edges > 0 && !d_weights) return COOP_EINVAL;
   return launch_run<MODE_SSSP>(c, g, d_weights, source, nullptr, d_dist, (cudaStream_t)stream, stats, true, 0, 0);
+}
+
+coop_status coop_sssp_topo(coop_ctx *c, const coop_csr *g, const uint32_t *d_weights, int32_t source,
+                           uint32_t *d_dist, coop_stream stream, coop_stats *stats) {
+  if (!c || !d_dist) return COOP_EINVAL;
+  const coop_status st = check_graph(g, source);
+  if (st != COOP_OK) return st;
+  if (g->num_edges > 0 && !d_weights) return COOP_EINVAL;
+  return launch_run<MODE_PSSSP>(c, g, d_weights, source, nullptr, d_dist, (cudaStream_t)stream, stats, true, 0, 0);
 }
 
 coop_status coop_bfs_baseline(coop_ctx *c, const coop_csr *g, int32_t source, int32_t *d_levels,

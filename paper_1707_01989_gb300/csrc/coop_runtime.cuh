@@ -57,7 +57,9 @@ constexpr uint32_t kChunkUnitsMax = 16;     // a work chunk spans 1..16 32-edge 
 // round trip on the level's critical path, and the claim goes straight to the atomic.
 constexpr uint32_t kPrecheckEdges = 65536;
 
-enum Mode : int { MODE_BFS = 0, MODE_SSSP = 1, MODE_BARRIER = 2 };
+// MODE_PSSSP: topology-driven SSSP (Table 1's p-sssp, read as Pannotia's formulation):
+// every iteration scans all vertices in three intervals -- relax, update, check.
+enum Mode : int { MODE_BFS = 0, MODE_SSSP = 1, MODE_BARRIER = 2, MODE_PSSSP = 3 };
 
 // Where the host's requests for CTAs are served (Sec. 4.2, "An Efficient Resizing Barrier"):
 //  KILL_CHUNK   the query barrier, plus a kill point between two chunks of an interval
@@ -423,7 +425,10 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
   // Everything else the release needs, in one batch of independent loads: the output
   // queue's counters and the releaser-private books.
   const uint32_t out = cur.sel ^ 1u;
-  const unsigned long long packed = (MODE == MODE_BARRIER) ? 0ull : c->qctr[out];
+  // the output queue's (vertices << 32 | edges); topology-driven SSSP: the vertices its
+  // update interval lowered, and the edges its relax interval scanned
+  const unsigned long long packed = (MODE == MODE_BARRIER) ? 0ull : (MODE == MODE_PSSSP) ? c->qctr[0] : c->qctr[out];
+  const unsigned long long relaxed = (MODE == MODE_PSSSP) ? c->qctr[1] : 0ull;
   const uint32_t A = c->admitted;
   const uint32_t decided = c->host_decided;
   const int32_t barriers = c->barriers + 1, kills0 = c->kills, forks0 = c->forks;
@@ -448,6 +453,16 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
   if (MODE == MODE_BARRIER) {
     count = (cur.level + 1 < p.n_barriers) ? 1u : 0u;
     edges = 0u;
+  } else if (MODE == MODE_PSSSP) {
+    // intervals relax, update, check: after the check, stop if the update lowered nothing
+    count = 1u;
+    edges = 0u;
+    if ((uint32_t)cur.level % 3u == 2u) {
+      count = (uint32_t)packed;
+      edges = (uint32_t)relaxed;
+      c->qctr[0] = 0ull;
+      c->qctr[1] = 0ull;
+    }
   } else {
     count = (uint32_t)(packed >> 32);
     edges = (uint32_t)packed;
@@ -651,12 +666,18 @@ __device__ __forceinline__ void master_enter(const Params &p, CtaShared &cs) {
       if (MODE == MODE_BFS) {
         p.level[s] = 0;
         atomicOr(p.visited + (s >> 5), 1u << (s & 31));
-      } else {
+      } else if (MODE == MODE_SSSP) {
         p.ds[s] = 1ull;  // distance 0, queued for round 1
+      } else {
+        p.dist[s] = 0u;  // topology-driven: distance 0, cost 0, changed
+        reinterpret_cast<uint32_t *>(p.ds)[s] = 0u;
+        atomicOr(p.visited + (s >> 5), 1u << (s & 31));
       }
       c->reached = 1ull;
       c->reached_edges = (unsigned long long)(re - rs);
-      if (re > rs) {
+      if (MODE == MODE_PSSSP) {
+        count = 1u;  // the iterations run until one lowers nothing
+      } else if (re > rs) {
         p.qo[0][0] = 0u;
         p.qs[0][0] = (uint32_t)rs;
         p.qv[0][0] = (uint32_t)s;

@@ -288,3 +288,19 @@ def test_kill_modes_serve_requests(ctx, mode):
 def test_kill_mode_rejects_unknown(ctx):
     with pytest.raises(coop.CoopError):
         coop.coop_set_kill_mode(ctx, 3)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_topology_driven_sssp_under_schedules(ctx, seed):
+    """p-sssp under forced kill/fork schedules and host requests: bit-exact, legal log."""
+    g = gg.rmat(12, 16, seed=40 + seed)
+    w = gg.weights(g, 41 + seed)
+    src = gg.max_out_degree_vertex(g)
+    dg = DevGraph(g, w)
+    coop.coop_set_schedule(ctx, 500 + seed, p_kill=0.3, p_fork=0.4)
+    out = dg.empty()
+    st = coop.coop_sssp_topo(ctx, dg.csr, dg.w, src, out, stats=True)
+    coop.coop_set_schedule(ctx, 0, 0.0, 0.0)
+    assert_same(out.cpu().numpy().view(np.uint32), oracle.dijkstra(g, w, src), f"p-sssp schedule {seed}")
+    assert st.kills > 0 or st.forks > 0
+    _replay(ctx, st)

@@ -200,3 +200,45 @@ def test_full_size_rmat22_bfs(ctx):
     exp = oracle.bfs(g, src)
     assert_same(lv, exp, "rmat22 bfs")
     assert st.edges_scanned == oracle.traversal_work(g, exp >= 0)[1]
+
+
+def _run_topo(ctx, dg, src, ok=(coop.COOP_OK,)):
+    out = dg.empty()
+    out.fill_(0x5A5A5A5A)
+    st = coop.coop_sssp_topo(ctx, dg.csr, dg.w, src, out, stats=True, ok=ok)
+    return out.cpu().numpy().view(np.uint32), st
+
+
+@pytest.mark.parametrize("name", ["rmat13", "grid", "random", "path", "star", "no_out_edges"])
+def test_topology_driven_sssp_matches_oracle(ctx, name):
+    """p-sssp (Table 1): three barriers per iteration, same distances as Dijkstra."""
+    if name == "rmat13":
+        g = gg.rmat(13, 16, seed=31)
+        src = gg.max_out_degree_vertex(g)
+    elif name == "grid":
+        g, src = gg.grid(50, 40), 0
+    elif name == "random":
+        g = gg.random_graph(3000, 24000, seed=32)
+        src = 7
+    elif name == "path":
+        g, src = gg.path(300), 0
+    elif name == "star":
+        g, src = gg.star(500), 0
+    else:
+        g = gg.rmat(12, 8, seed=33)
+        src = int(np.flatnonzero(np.diff(np.array(g.row_off)) == 0)[0])
+    w = gg.weights(g, 34)
+    dg = DevGraph(g, w)
+    d, st = _run_topo(ctx, dg, src)
+    exp = oracle.dijkstra(g, w, src)
+    assert_same(d, exp, f"p-sssp {name}")
+    assert st.barriers % 3 == 0  # whole iterations: relax, update, check
+    assert st.vertices_reached == int((exp != 0xFFFFFFFF).sum())
+    assert st.reached_edges == oracle.traversal_work(g, exp != 0xFFFFFFFF)[1]
+
+
+def test_topology_driven_sssp_overflow_reported(ctx):
+    g = gg.path(4)
+    w = np.array([0xFFFFFFF0, 0xFFFFFFF0, 1], dtype=np.uint32)
+    d, st = _run_topo(ctx, DevGraph(g, w), 0, ok=(coop.COOP_EOVERFLOW,))
+    assert st.status == coop.COOP_EOVERFLOW
