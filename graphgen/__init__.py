@@ -190,3 +190,24 @@ def max_out_degree_vertex(g: CSR) -> int:
 def default_rmat_config(scale: int):
     """The R-MAT workloads: (graph seed, weight seed) per scale (20 -> 20/21, 22 -> 22/23)."""
     return scale, scale + 1
+
+
+def points(n: int, seed: int, kind: str = "clustered"):
+    """n points with integer coordinates in [0, 2^21)^3, the octree workload's input, as
+    three uint32 arrays.  'uniform': independent uniform coordinates (a shallow, even
+    tree); 'clustered': 16 Gaussian clusters with random centres and widths from 2^8 to
+    2^18, clipped to the cube (deep, uneven trees, like the particle sets octrees are
+    built for)."""
+    rng = np.random.default_rng(seed)
+    hi = 1 << 21
+    if kind == "uniform":
+        return tuple(rng.integers(0, hi, n, dtype=np.uint32) for _ in range(3))
+    if kind != "clustered":
+        raise ValueError(kind)
+    k = 16
+    centres = rng.integers(0, hi, (k, 3)).astype(np.float64)
+    widths = 2.0 ** rng.uniform(8.0, 18.0, k)
+    lab = rng.integers(0, k, n)
+    pts = centres[lab] + rng.normal(0.0, 1.0, (n, 3)) * widths[lab, None]
+    pts = np.clip(np.rint(pts), 0, hi - 1).astype(np.uint32)
+    return np.ascontiguousarray(pts[:, 0]), np.ascontiguousarray(pts[:, 1]), np.ascontiguousarray(pts[:, 2])
