@@ -331,6 +331,34 @@ coop_status coop_server_release(coop_server *sv, int n_ctas);
 /* Drain the queue, wait for running queries and free everything.  NULL is a no-op. */
 coop_status coop_server_destroy(coop_server *sv);
 
+/* ---- octree partitioning (work stealing) ---- */
+
+/*
+ * Octree partitioning of n points, the work-stealing application of Table 1 (Sec. 2.2
+ * Fig. 2; Sec. 3.2 "Adapting Work Stealing"), run as a cooperative kernel on this
+ * context: per-CTA task queues guarded by compare-and-swap mutexes, stealing from other
+ * queues, offer_kill at the head of the main loop and forked CTAs taking queues of
+ * their own -- coop_request_resources / coop_release apply while it runs.
+ *
+ * d_x, d_y, d_z: uint32[n] device coordinates, each below 2^21 (else COOP_EGRAPH).  The
+ * root cell is the cube [0, 2^21)^3 at depth 0; a cell at depth d < max_depth (0..21)
+ * holding more than leaf_cap (>= 1) points splits into its octants by coordinate bit
+ * 20 - d (octant = bx | by << 1 | bz << 2); every other non-empty cell is a leaf.  Output
+ * (caller-owned device memory): *d_n_leaves leaves, leaf i with path code d_leaf_code[i]
+ * (a 1 followed by 3 bits per level below the root) holding the d_leaf_count[i] point
+ * indices d_perm[d_leaf_begin[i] .. + count); d_perm is uint32[n], the leaf arrays hold
+ * max_leaves entries (n always suffices).  The leaves and each leaf's point set are
+ * unique; their order in memory is not.  Asynchronous unless stats is non-NULL; with
+ * stats: kills, forks, initial_active, ctas_launched as for traversals, frontier_total =
+ * tasks processed, edges_scanned = steals, vertices_reached = leaves, reached_edges =
+ * points moved by partitioning.  COOP_EOVERFLOW if more than max_leaves leaves or a task
+ * queue overflowed; COOP_ETIMEOUT on a device wait beyond coop_set_timeout.
+ */
+coop_status coop_octree(coop_ctx *ctx, const uint32_t *d_x, const uint32_t *d_y, const uint32_t *d_z, int32_t n,
+                        int32_t leaf_cap, int32_t max_depth, uint64_t *d_leaf_code, uint32_t *d_leaf_begin,
+                        uint32_t *d_leaf_count, int32_t max_leaves, uint32_t *d_perm, int32_t *d_n_leaves,
+                        coop_stream stream, coop_stats *stats);
+
 /*
  * The co-running latency-critical task: y[i] = a * x[i] + y[i] for i < n (fp32,
  * device pointers), on n_ctas CTAs whose shared-memory reservation keeps them off any

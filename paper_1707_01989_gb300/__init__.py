@@ -19,7 +19,7 @@ from . import _build
 
 __all__ = [
     "CoopError", "CoopUnavailable", "Stats", "CSR", "coop_init", "coop_destroy", "coop_bfs", "coop_sssp",
-    "coop_sssp_topo",
+    "coop_sssp_topo", "coop_octree",
     "coop_request_resources", "coop_release", "coop_sync", "coop_get_stats", "coop_get_resize_log",
     "coop_set_schedule", "coop_set_timeout", "coop_set_timing", "coop_set_kill_mode", "COOP_KILL_CHUNK",
     "COOP_KILL_QUERY", "COOP_KILL_SIMPLE", "coop_query", "coop_bfs_baseline", "coop_sssp_baseline",
@@ -111,6 +111,7 @@ def load_library():
                 "coop_bfs": [vp, cp, i32, vp, vp, sp],
                 "coop_sssp": [vp, cp, vp, i32, vp, vp, sp],
                 "coop_sssp_topo": [vp, cp, vp, i32, vp, vp, sp],
+                "coop_octree": [vp, vp, vp, vp, i32, i32, i32, vp, vp, vp, i32, vp, vp, vp, sp],
                 "coop_bfs_baseline": [vp, cp, i32, vp, vp, sp],
                 "coop_sssp_baseline": [vp, cp, vp, i32, vp, vp, sp],
                 "coop_request_resources": [vp, ctypes.c_int, ctypes.c_int, ip],
@@ -272,6 +273,22 @@ def coop_sssp_topo(ctx, g: CSR, weights, source: int, dist, stream=None, stats: 
     st = load_library().coop_sssp_topo(_h(ctx), ctypes.byref(g), _ptr(weights, None, g.num_edges, "weights"),
                                        int(source), _ptr(dist, None, g.num_vertices, "dist"), _stream(stream), sp)
     _check(st, "coop_sssp_topo", ok)
+    return s
+
+
+def coop_octree(ctx, x, y, z, leaf_cap: int, max_depth: int, leaf_code, leaf_begin, leaf_count, perm, n_leaves,
+                stream=None, stats: bool = False, ok=(COOP_OK,)):
+    """Octree partitioning of the points (x, y, z) (uint32 device tensors, coordinates
+    below 2^21); leaves into leaf_code (int64/uint64), leaf_begin, leaf_count, perm
+    (int32/uint32) and n_leaves (one int32).  See include/coop.h."""
+    n = x.numel()
+    s, sp = _stats_ptr(stats)
+    st = load_library().coop_octree(
+        _h(ctx), _ptr(x, None, n, "x"), _ptr(y, None, n, "y"), _ptr(z, None, n, "z"), int(n), int(leaf_cap),
+        int(max_depth), _ptr(leaf_code, None, 0, "leaf_code"), _ptr(leaf_begin, None, 0, "leaf_begin"),
+        _ptr(leaf_count, None, 0, "leaf_count"), int(leaf_code.numel()), _ptr(perm, None, n, "perm"),
+        _ptr(n_leaves, None, 1, "n_leaves"), _stream(stream), sp)
+    _check(st, "coop_octree", ok)
     return s
 
 

@@ -845,6 +845,379 @@ __global__ void __launch_bounds__(1024) coop_saxpy_kernel(int64_t n, float a, co
 
 }  // namespace
 
+// ===================================================================== octree (work stealing)
+// Octree partitioning, the work-stealing application of Table 1 (Sec. 2.2 Fig. 2 and
+// Sec. 3.2 "Adapting Work Stealing").  A task is a cell: a range of points and the cell's
+// path code (a 1 followed by 3 bits per level).  A CTA pops a task from its own queue
+// (newest first, so the queue stays short) or steals one from another queue (oldest
+// first); a cell holding more than leaf_cap points (and above max_depth) is partitioned
+// into its octants by coordinate bit 20 - depth, into the other of two buffers, and its
+// non-empty octants are pushed as new tasks; any other cell is a leaf.  Every queue is
+// guarded by a mutex (compare-and-swap).  There are no barriers: offer_kill sits at the
+// head of the main loop (a leaving CTA's queued tasks are stolen by the others) and the
+// master's scheduler warp launches forked CTAs, which take a queue slot of their own.
+namespace {
+
+struct OctTask {
+  uint32_t begin, count;
+  unsigned long long code;  // leading 1 at bit 3 * depth, then the octants from the root
+};
+constexpr uint32_t kOctQueues = 256;      // queue slots; CTAs take them in arrival order
+constexpr uint32_t kOctQueueCap = 1024;   // tasks per queue (depth-first pops: ~7 per level)
+
+struct alignas(128) OctQueue {
+  uint32_t lock;  // 0 free, 1 held
+  uint32_t head;  // thieves take from here
+  uint32_t tail;  // the owner pushes and pops here
+  uint32_t pad[29];
+};
+
+struct OctCtl {  // zeroed by the init kernel
+  Word outstanding;  // tasks pushed and not yet completed
+  Word slots;        // queue slots handed out
+  Word leaves;       // leaf records written
+  Word done;
+  Word err;
+  Word killed;       // CTAs that left at offer_kill
+  Word host_req;     // the host's requests of this run (scheduler warp)
+  Word launched;     // CTAs launched (main grid + forks)
+  alignas(128) unsigned long long tasks, steals, moved;
+};
+
+struct OctParams {
+  const uint32_t *x, *y, *z;  // caller's coordinates
+  uint32_t *bx[2], *by[2], *bz[2], *bi[2];  // ping-pong: coordinates and point index
+  uint32_t *perm;             // out: point indices, each leaf's points in its range
+  unsigned long long *leaf_code;
+  uint32_t *leaf_begin, *leaf_count;
+  int32_t *n_leaves;
+  uint32_t max_leaves;
+  OctQueue *queues;
+  OctTask *tasks;
+  OctCtl *ctl;
+  Mailbox *mbox;
+  uint32_t n, leaf_cap, max_depth;
+  uint32_t launched, kill_base, fork_base, coop;
+  uint64_t timeout_ns;
+};
+
+__device__ __forceinline__ void oct_error(const OctParams &p, int code) {
+  atomicCAS(&p.ctl->err.v, 0u, (uint32_t)code);
+}
+
+__device__ __forceinline__ bool oct_lock(const OctParams &p, uint32_t q) {
+  uint32_t *l = &p.queues[q].lock;
+  const uint64_t t0 = gtime();
+  for (uint32_t spin = 0;; ++spin) {
+    if (ld_relaxed(l) == 0u && atomicCAS(l, 0u, 1u) == 0u) {
+      __threadfence();  // acquire: the queue's tasks and what they describe
+      return true;
+    }
+    if ((spin & 63u) == 63u && (gtime() - t0 > p.timeout_ns || ld_relaxed(&p.ctl->err.v) != 0u)) {
+      oct_error(p, ERR_TIMEOUT);
+      return false;
+    }
+    __nanosleep(32);
+  }
+}
+
+__device__ __forceinline__ void oct_unlock(const OctParams &p, uint32_t q) {
+  __threadfence();
+  st_release(&p.queues[q].lock, 0u);
+}
+
+// Take a task from queue q: its newest (own queue) or its oldest (a steal).
+__device__ __forceinline__ bool oct_pop(const OctParams &p, uint32_t q, bool own, OctTask &t) {
+  OctQueue &Q = p.queues[q];
+  if (ld_relaxed(&Q.tail) == ld_relaxed(&Q.head)) return false;  // hint, without the lock
+  if (!oct_lock(p, q)) return false;
+  const uint32_t h = ld_relaxed(&Q.head), tl = ld_relaxed(&Q.tail);
+  bool ok = false;
+  if (tl != h) {
+    const uint32_t at = own ? tl - 1u : h;
+    t = p.tasks[(size_t)q * kOctQueueCap + at % kOctQueueCap];
+    if (own) st_relaxed(&Q.tail, tl - 1u);
+    else st_relaxed(&Q.head, h + 1u);
+    ok = true;
+  }
+  oct_unlock(p, q);
+  return ok;
+}
+
+__device__ __forceinline__ bool oct_push(const OctParams &p, uint32_t q, const OctTask *c, uint32_t n) {
+  OctQueue &Q = p.queues[q];
+  if (!oct_lock(p, q)) return false;
+  const uint32_t h = ld_relaxed(&Q.head), tl = ld_relaxed(&Q.tail);
+  const bool ok = tl - h + n <= kOctQueueCap;
+  if (ok) {
+    for (uint32_t i = 0; i < n; ++i) p.tasks[(size_t)q * kOctQueueCap + (tl + i) % kOctQueueCap] = c[i];
+    st_relaxed(&Q.tail, tl + n);
+  }
+  oct_unlock(p, q);
+  if (!ok) oct_error(p, ERR_OVERFLOW);
+  return ok;
+}
+
+__device__ __forceinline__ uint32_t octant(uint32_t x, uint32_t y, uint32_t z, uint32_t b) {
+  return ((x >> b) & 1u) | (((y >> b) & 1u) << 1) | (((z >> b) & 1u) << 2);
+}
+
+template <int NW>
+__global__ void __launch_bounds__((NW + 1) * 32, 1) coop_octree_kernel(const __grid_constant__ OctParams p, int join);
+
+// The scheduler side for the octree (master CTA only): mirrors the host's requests for
+// the CTAs' offer_kill, reports CTAs that left, launches the CTAs the host gives back.
+template <int NW>
+__device__ void oct_scheduler(const OctParams &p, const volatile int32_t *workers_left) {
+  OctCtl *c = p.ctl;
+  uint32_t forks_seen = p.fork_base, freed_seen = 0u, req_seen = 0u;
+  for (;;) {
+    const uint64_t req = ld_sys64(&p.mbox->kill_req);
+    const uint32_t r = (uint32_t)req - p.kill_base, f = (uint32_t)(req >> 32);
+    if (r != req_seen) {
+      req_seen = r;
+      st_relaxed(&c->host_req.v, r);
+    }
+    const uint32_t k = ld_relaxed(&c->killed.v);
+    if (k != freed_seen) {
+      st_sys(&p.mbox->freed, p.kill_base + k);
+      freed_seen = k;
+    }
+    if ((int32_t)(f - forks_seen) > 0) {
+      const uint32_t n = f - forks_seen;
+      forks_seen = f;
+      atomicAdd(&c->launched.v, n);
+      coop_octree_kernel<NW><<<n, (NW + 1) * 32, kTraverseSmemMin, cudaStreamFireAndForget>>>(p, 1);
+    }
+    if (ld_relaxed(&c->done.v) != 0u || ld_relaxed(&c->err.v) != 0u || *workers_left != 0) return;
+    __nanosleep(200);
+  }
+}
+
+template <int NW>
+__global__ void __launch_bounds__((NW + 1) * 32, 1) coop_octree_kernel(const __grid_constant__ OctParams p, int join) {
+  extern __shared__ __align__(16) unsigned char oct_reserve[];  // SM-exclusivity reservation only
+  (void)oct_reserve;
+  __shared__ OctTask s_task;
+  __shared__ int32_t s_state, s_workers_left;
+  __shared__ uint32_t s_slot, s_hist[8], s_off[8], s_cur[8];
+  OctCtl *c = p.ctl;
+  const bool master = !join && blockIdx.x == 0;
+  const unsigned tid = threadIdx.x, lane = tid & 31u;
+  constexpr uint32_t T = NW * 32;
+  if (tid == 0) {
+    s_slot = atomicAdd(&c->slots.v, 1u) % kOctQueues;
+    s_workers_left = 0;
+  }
+  __syncthreads();
+  if (tid >= T) {
+    if (master && p.coop && tid == T) oct_scheduler<NW>(p, &s_workers_left);
+    return;
+  }
+  uint64_t idle0 = 0;
+  for (;;) {
+    if (tid == 0) {
+      int st = 0;
+      // offer_kill at the head of the main loop; the master never leaves
+      if (p.coop && !master) {
+        uint32_t k = ld_relaxed(&c->killed.v);
+        while (k < ld_relaxed(&c->host_req.v)) {
+          const uint32_t prev = atomicCAS(&c->killed.v, k, k + 1u);
+          if (prev == k) {
+            st = 2;
+            break;
+          }
+          k = prev;
+        }
+      }
+      if (st == 0) {
+        OctTask t;
+        if (oct_pop(p, s_slot, true, t)) {
+          st = 1;
+        } else {
+          // steal: every other queue in use, starting after this CTA's own
+          const uint32_t nq = min(ld_relaxed(&c->slots.v), kOctQueues);
+          for (uint32_t i = 1; i < nq && st == 0; ++i) {
+            if (oct_pop(p, (s_slot + i) % nq, false, t)) {
+              st = 1;
+              atomicAdd(&c->steals, 1ull);
+            }
+          }
+        }
+        if (st == 1) {
+          s_task = t;
+          idle0 = 0;
+        } else if (ld_acquire(&c->outstanding.v) == 0u || ld_relaxed(&c->done.v) != 0u ||
+                   ld_relaxed(&c->err.v) != 0u) {
+          st = 3;
+        } else {
+          const uint64_t now = gtime();
+          if (idle0 == 0) idle0 = now;
+          if (now - idle0 > p.timeout_ns) {
+            oct_error(p, ERR_TIMEOUT);
+            st = 3;
+          } else {
+            // nothing to steal yet: back off (up to ~4 us) so idle CTAs leave the queue
+            // headers to the working ones
+            const uint64_t back = 200ull + (now - idle0) / 8ull;
+            __nanosleep(back < 4000ull ? (unsigned)back : 4000u);
+          }
+        }
+      }
+      s_state = st;
+    }
+    workers_sync<NW>();
+    const int st = s_state;
+    if (st >= 2) {
+      if (tid == 0 && st == 2) __threadfence();
+      break;
+    }
+    if (st == 1) {
+      const OctTask t = s_task;
+      const uint32_t d = (uint32_t)(63 - __clzll((long long)t.code)) / 3u;
+      const uint32_t src = d & 1u, dst = src ^ 1u;
+      if (t.count <= p.leaf_cap || d >= p.max_depth) {
+        for (uint32_t i = tid; i < t.count; i += T) p.perm[t.begin + i] = __ldcg(p.bi[src] + t.begin + i);
+        if (tid == 0) {
+          const uint32_t li = atomicAdd(&c->leaves.v, 1u);
+          if (li < p.max_leaves) {
+            p.leaf_code[li] = t.code;
+            p.leaf_begin[li] = t.begin;
+            p.leaf_count[li] = t.count;
+          } else {
+            oct_error(p, ERR_OVERFLOW);
+          }
+          s_hist[0] = 0xFFFFFFFFu;  // marks a leaf: no children
+        }
+      } else {
+        // partition by the octant at this depth: histogram, offsets, scatter (ballots
+        // aggregate each warp's points per octant; shared-memory atomics per warp)
+        const uint32_t b = 20u - d;
+        if (tid < 8) s_hist[tid] = 0u;
+        workers_sync<NW>();
+        bool bad = false;
+        for (uint32_t i0 = 0; i0 < t.count; i0 += T) {
+          const uint32_t i = i0 + tid;
+          uint32_t o = 8u;
+          if (i < t.count) {
+            const uint32_t x = __ldcg(p.bx[src] + t.begin + i), y = __ldcg(p.by[src] + t.begin + i),
+                           z = __ldcg(p.bz[src] + t.begin + i);
+            if ((x | y | z) >> 21) bad = true;
+            o = octant(x, y, z, b);
+          }
+#pragma unroll
+          for (uint32_t k = 0; k < 8u; ++k) {
+            const unsigned m = __ballot_sync(kFull, o == k);
+            if (lane == 0 && m) atomicAdd(&s_hist[k], (uint32_t)__popc(m));
+          }
+        }
+        if (bad) oct_error(p, ERR_GRAPH);
+        workers_sync<NW>();
+        if (tid == 0) {
+          uint32_t acc = 0u;
+          for (int k = 0; k < 8; ++k) {
+            s_off[k] = acc;
+            s_cur[k] = acc;
+            acc += s_hist[k];
+          }
+        }
+        workers_sync<NW>();
+        const unsigned lt = lanemask_lt();
+        for (uint32_t i0 = 0; i0 < t.count; i0 += T) {
+          const uint32_t i = i0 + tid;
+          uint32_t o = 8u, x = 0u, y = 0u, z = 0u, id = 0u;
+          if (i < t.count) {
+            x = __ldcg(p.bx[src] + t.begin + i);
+            y = __ldcg(p.by[src] + t.begin + i);
+            z = __ldcg(p.bz[src] + t.begin + i);
+            id = __ldcg(p.bi[src] + t.begin + i);
+            o = octant(x, y, z, b) & 7u;
+          }
+          uint32_t pos = 0u;
+#pragma unroll
+          for (uint32_t k = 0; k < 8u; ++k) {
+            const unsigned m = __ballot_sync(kFull, o == k && i < t.count);
+            if (m) {
+              const unsigned first = (unsigned)__ffs(m) - 1u;
+              uint32_t base = 0u;
+              if (lane == first) base = atomicAdd(&s_cur[k], (uint32_t)__popc(m));
+              base = __shfl_sync(kFull, base, first);
+              if (o == k && i < t.count) pos = base + (uint32_t)__popc(m & lt);
+            }
+          }
+          if (i < t.count) {
+            const uint32_t at = t.begin + pos;
+            p.bx[dst][at] = x;
+            p.by[dst][at] = y;
+            p.bz[dst][at] = z;
+            p.bi[dst][at] = id;
+          }
+        }
+      }
+      __threadfence();  // this CTA's writes before the tasks that will read them
+      workers_sync<NW>();
+      if (tid == 0) {
+        OctTask ch[8];
+        uint32_t nc = 0u;
+        if (s_hist[0] != 0xFFFFFFFFu) {
+          for (uint32_t k = 0; k < 8u; ++k)
+            if (s_hist[k]) ch[nc++] = OctTask{t.begin + s_off[k], s_hist[k], (t.code << 3) | k};
+          atomicAdd(&c->moved, (unsigned long long)t.count);
+        }
+        bool ok = true;
+        if (nc) ok = oct_push(p, s_slot, ch, nc);
+        atomicAdd(&c->tasks, 1ull);
+        if (ok) {
+          // this task is done and nc are new: the run ends when none is outstanding
+          const uint32_t prev = atomicAdd(&c->outstanding.v, nc - 1u);
+          if (prev + nc - 1u == 0u) st_release(&c->done.v, 1u);
+        }
+      }
+    }
+    workers_sync<NW>();  // s_state and s_task are rewritten only after every worker read them
+  }
+  if (tid == 0) *(volatile int32_t *)&s_workers_left = 1;
+}
+
+__global__ void __launch_bounds__(512) coop_octree_init(const __grid_constant__ OctParams p) {
+  const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = tid; i < p.n; i += nth) {
+    p.bx[0][i] = p.x[i];
+    p.by[0][i] = p.y[i];
+    p.bz[0][i] = p.z[i];
+    p.bi[0][i] = (uint32_t)i;
+  }
+  if (tid == 0) {
+    uint32_t *cw = reinterpret_cast<uint32_t *>(p.ctl);
+    for (size_t i = 0; i < sizeof(OctCtl) / 4; ++i) cw[i] = 0u;
+    for (uint32_t q = 0; q < kOctQueues; ++q) {
+      p.queues[q].lock = 0u;
+      p.queues[q].head = 0u;
+      p.queues[q].tail = 0u;
+    }
+    p.tasks[0] = OctTask{0u, p.n, 1ull};  // the root cell, in queue 0
+    p.queues[0].tail = 1u;
+    p.ctl->outstanding.v = 1u;
+    p.ctl->launched.v = p.launched;
+    *p.n_leaves = 0;
+  }
+}
+
+__global__ void coop_octree_finish(const __grid_constant__ OctParams p) {
+  *p.n_leaves = (int32_t)min(p.ctl->leaves.v, p.max_leaves);
+}
+
+const void *octree_fn(int nw) {
+  switch (nw) {
+    case 31: return (const void *)coop_octree_kernel<31>;
+    case 23: return (const void *)coop_octree_kernel<23>;
+    default: return (const void *)coop_octree_kernel<15>;
+  }
+}
+
+
+}  // namespace
+
 // ===================================================================== host side
 
 struct coop_ctx {
@@ -856,6 +1229,8 @@ struct coop_ctx {
   cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;  // kernel timing (optional)
   bool timing = false;
   uint32_t kill_mode = 0;  // KILL_CHUNK
+  void *oct_scratch = nullptr;  // octree: buffers, queues, tasks, control block
+  int64_t oct_cap = 0;
   Mailbox *mbox = nullptr;    // host view
   Mailbox *mbox_d = nullptr;  // device view of the same pinned page
   Ctl *ctl = nullptr;
@@ -1138,6 +1513,7 @@ coop_status coop_init(int device, int max_ctas, int threads_per_cta, coop_ctx **
                                        kCorunnerSmem),
                   "set co-runner smem"))
     return fail(COOP_ECUDA);
+  if (!set_traverse_attrs(octree_fn(nw), kTraverseSmemMin)) return fail(COOP_ECUDA);
   if (per_sm < 1) {
     snprintf(g_last_error, sizeof(g_last_error), "traversal kernel cannot be resident (%d per SM)", per_sm);
     return fail(COOP_ECUDA);
@@ -1147,7 +1523,8 @@ coop_status coop_init(int device, int max_ctas, int threads_per_cta, coop_ctx **
   // while a traversal runs would not start until the traversal ended.
   {
     const void *all[] = {traverse_fn<MODE_BFS>(nw), traverse_fn<MODE_SSSP>(nw), traverse_fn<MODE_BARRIER>(nw),
-                         traverse_fn<MODE_PSSSP>(nw), (const void *)coop_init_kernel<MODE_PSSSP>,
+                         traverse_fn<MODE_PSSSP>(nw), (const void *)coop_init_kernel<MODE_PSSSP>, octree_fn(nw),
+                         (const void *)coop_octree_init, (const void *)coop_octree_finish,
                          (const void *)coop_init_kernel<MODE_BFS>, (const void *)coop_init_kernel<MODE_SSSP>,
                          (const void *)coop_init_kernel<MODE_BARRIER>, (const void *)coop_saxpy_kernel};
     for (const void *k : all) {
@@ -1185,6 +1562,7 @@ coop_status coop_destroy(coop_ctx *c) {
   DeviceGuard guard(c->device);
   if (c->ev_done && c->launched) cudaEventSynchronize(c->ev_done);
   if (c->scratch) cudaFree(c->scratch);
+  if (c->oct_scratch) cudaFree(c->oct_scratch);
   if (c->ctl) cudaFree(c->ctl);
   if (c->mbox) cudaFreeHost(c->mbox);
   if (c->ev_done) cudaEventDestroy(c->ev_done);
@@ -2220,3 +2598,141 @@ extern "C" coop_status coop_bfs_noalloc(const coop_csr *g, int32_t source, int32
   if (cuda_failed(cudaGetLastError(), "allocation-free launch")) return COOP_ECUDA;
   return COOP_OK;
 }
+
+// ===================================================================== octree host side
+namespace {
+
+// Octree scratch for n points: 2 x 4 arrays of n words (coordinates and point index),
+// the queue headers, the task slots and the control block; grown to the largest n.
+coop_status ensure_oct_scratch(coop_ctx *c, int64_t n) {
+  if (n <= c->oct_cap && c->oct_scratch) return COOP_OK;
+  if (c->oct_scratch) {
+    if (c->launched) cudaEventSynchronize(c->ev_done);
+    cudaFree(c->oct_scratch);
+    c->oct_scratch = nullptr;
+    c->oct_cap = 0;
+  }
+  const int64_t cap = std::max<int64_t>(n, 1024);
+  const size_t words = ((size_t)cap * 4 + 255) & ~(size_t)255;
+  const size_t total = 8 * words + sizeof(OctQueue) * kOctQueues + sizeof(OctTask) * kOctQueues * kOctQueueCap +
+                       sizeof(OctCtl) + 1024;
+  if (cudaMalloc(&c->oct_scratch, total) != cudaSuccess) {
+    (void)cudaGetLastError();
+    c->oct_scratch = nullptr;
+    return COOP_ENOMEM;
+  }
+  c->oct_cap = cap;
+  return COOP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+coop_status coop_octree(coop_ctx *c, const uint32_t *d_x, const uint32_t *d_y, const uint32_t *d_z, int32_t n,
+                        int32_t leaf_cap, int32_t max_depth, uint64_t *d_leaf_code, uint32_t *d_leaf_begin,
+                        uint32_t *d_leaf_count, int32_t max_leaves, uint32_t *d_perm, int32_t *d_n_leaves,
+                        coop_stream stream, coop_stats *stats) {
+  if (!c || n < 0 || leaf_cap < 1 || max_depth < 0 || max_depth > 21 || !d_n_leaves) return COOP_EINVAL;
+  if (n > 0 && (!d_x || !d_y || !d_z || !d_leaf_code || !d_leaf_begin || !d_leaf_count || !d_perm ||
+                max_leaves < 1))
+    return COOP_EINVAL;
+  DeviceGuard guard(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> launch_lk(c->launch_mu);
+  if (c->launched) cudaEventSynchronize(c->ev_done);
+  OctParams p{};
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    finalize_locked(c);
+    if (n == 0) {
+      if (cuda_failed(cudaMemsetAsync(d_n_leaves, 0, sizeof(int32_t), s), "octree: empty")) return COOP_ECUDA;
+      if (stats) {
+        if (cudaStreamSynchronize(s) != cudaSuccess) return COOP_ECUDA;
+        memset(stats, 0, sizeof(*stats));
+      }
+      return COOP_OK;
+    }
+    coop_status st = ensure_oct_scratch(c, n);
+    if (st != COOP_OK) return st;
+    char *base = static_cast<char *>(c->oct_scratch);
+    const size_t words = ((size_t)c->oct_cap * 4 + 255) & ~(size_t)255;
+    uint32_t *w[8];
+    for (int i = 0; i < 8; ++i) w[i] = reinterpret_cast<uint32_t *>(base + (size_t)i * words);
+    char *at = base + 8 * words;
+    p.queues = reinterpret_cast<OctQueue *>(at);
+    at += sizeof(OctQueue) * kOctQueues;
+    p.tasks = reinterpret_cast<OctTask *>(at);
+    at += sizeof(OctTask) * kOctQueues * kOctQueueCap;
+    p.ctl = reinterpret_cast<OctCtl *>(((uintptr_t)at + 127) & ~(uintptr_t)127);
+    for (int b = 0; b < 2; ++b) {
+      p.bx[b] = w[4 * b];
+      p.by[b] = w[4 * b + 1];
+      p.bz[b] = w[4 * b + 2];
+      p.bi[b] = w[4 * b + 3];
+    }
+    p.x = d_x;
+    p.y = d_y;
+    p.z = d_z;
+    p.n = (uint32_t)n;
+    p.leaf_cap = (uint32_t)leaf_cap;
+    p.max_depth = (uint32_t)max_depth;
+    p.perm = d_perm;
+    p.leaf_code = reinterpret_cast<unsigned long long *>(d_leaf_code);
+    p.leaf_begin = d_leaf_begin;
+    p.leaf_count = d_leaf_count;
+    p.n_leaves = d_n_leaves;
+    p.max_leaves = (uint32_t)max_leaves;
+    p.mbox = c->mbox_d;
+    const int held = (int)(c->served - c->returned);
+    p.launched = (uint32_t)std::max(1, c->N - held);
+    p.kill_base = c->served;
+    p.fork_base = c->fork_req;
+    p.coop = 1u;
+    p.timeout_ns = (uint64_t)std::max<int64_t>(c->timeout_us, 1) * 1000ull;
+    c->mbox->err = 0;
+    store_release(&c->mbox->freed, c->served);
+    store_release(&c->mbox->kill_req, c->kill_req);
+    store_release(&c->mbox->fork_req, c->fork_req);
+    coop_octree_init<<<c->sm_count * 4, 512, 0, s>>>(p);
+    if (c->timing) cudaEventRecord(c->ev_t0, s);
+    switch (c->nw) {
+      case 31: coop_octree_kernel<31><<<p.launched, 32 * 32, kTraverseSmemMin, s>>>(p, 0); break;
+      case 23: coop_octree_kernel<23><<<p.launched, 24 * 32, kTraverseSmemMin, s>>>(p, 0); break;
+      default: coop_octree_kernel<15><<<p.launched, 16 * 32, kTraverseSmemMin, s>>>(p, 0); break;
+    }
+    if (c->timing) cudaEventRecord(c->ev_t1, s);
+    coop_octree_finish<<<1, 1, 0, s>>>(p);
+    cudaEventRecord(c->ev_done, s);
+    if (cuda_failed(cudaGetLastError(), "octree launch")) return COOP_ECUDA;
+    c->launched = true;
+    c->gather_us_max = 0.0;
+  }
+  if (!stats) return COOP_OK;
+  if (cuda_failed(cudaEventSynchronize(c->ev_done), "octree")) return COOP_ECUDA;
+  OctCtl h{};
+  if (cuda_failed(cudaMemcpy(&h, p.ctl, sizeof(h), cudaMemcpyDeviceToHost), "octree stats")) return COOP_ECUDA;
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    finalize_locked(c);
+  }
+  memset(stats, 0, sizeof(*stats));
+  stats->kills = (int32_t)h.killed.v;
+  stats->forks = (int32_t)(h.launched.v - p.launched);
+  stats->initial_active = (int32_t)p.launched;
+  stats->ctas_launched = (int32_t)h.launched.v;
+  stats->frontier_total = (int64_t)h.tasks;
+  stats->edges_scanned = (int64_t)h.steals;
+  stats->vertices_reached = (int64_t)h.leaves.v;
+  stats->reached_edges = (int64_t)h.moved;
+  if (c->timing) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev_t0, c->ev_t1) == cudaSuccess) stats->kernel_us = ms * 1e3;
+  }
+  int32_t status = (int32_t)h.err.v;
+  if (status == 0 && h.leaves.v > (uint32_t)max_leaves) status = COOP_EOVERFLOW;
+  stats->status = status;
+  return (coop_status)status;
+}
+
+}  // extern "C"
