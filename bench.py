@@ -652,6 +652,74 @@ def topology_driven(coop, ctx, dev, stream, flush, reps=3):
     return out
 
 
+def octree(coop, ctx, dev, stream, flush, n=1 << 22, leaf_cap=32, reps=3):
+    """The work-stealing application (Table 1 octree): build time of an octree over n
+    clustered points alone, then with the host taking half the CTAs every 5 ms (gather
+    time of the loop-head offer_kill), checked against the oracle."""
+    import numpy as np
+    import torch
+    import graphgen as gg
+    from oracle import octree as ot
+    pts = gg.points(n, 90, "clustered")
+    x, y, z = (torch.from_numpy(a.view(np.int32)).to(dev) for a in pts)
+    code = torch.empty(n, dtype=torch.int64, device=dev)
+    begin = torch.empty(n, dtype=torch.int32, device=dev)
+    count = torch.empty(n, dtype=torch.int32, device=dev)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    nl = torch.empty(1, dtype=torch.int32, device=dev)
+    run = lambda st: coop.coop_octree(ctx, x, y, z, leaf_cap, 21, code, begin, count, perm, nl, stream=stream,
+                                      stats=st)
+    run(False)
+    ks, st = [], None
+    for _ in range(reps):
+        flush.zero_()
+        st = run(True)
+        ks.append(st.kernel_us)
+    kus = statistics.median(ks)
+    k = int(nl.item())
+    c, b, cnt, pm = (a.cpu().numpy() for a in (code[:k], begin[:k], count[:k], perm))
+    got = np.zeros(n, dtype=np.uint64)
+    for cc, bb, kk in zip(c.view(np.uint64), b, cnt):
+        got[pm[bb:bb + kk]] = cc
+    t0 = time.perf_counter()
+    exp = ot.leaf_code_of_points(*pts, leaf_cap, 21)
+    cpu_s = time.perf_counter() - t0
+    out = {"points": n, "leaf_cap": leaf_cap, "leaves": k, "kernel_us": round(kus, 1),
+           "mpoints_per_s": round(n / (kus / 1e6) / 1e6, 1), "tasks": st.frontier_total, "steals": st.edges_scanned,
+           "points_moved": st.reached_edges, "bit_exact": bool(np.array_equal(got, exp)),
+           "oracle_s_1core": round(cpu_s, 3)}
+    # gather under the work-stealing loop's offer_kill
+    N = coop.coop_query(ctx)["max_ctas"]
+    gat = []
+    stop = threading.Event()
+
+    def ticker():
+        nxt = time.perf_counter()
+        while not stop.is_set():
+            t0 = time.perf_counter()
+            got_c = coop.coop_request_resources(ctx, N // 2, timeout_us=2_000_000)
+            gat.append((time.perf_counter() - t0) * 1e3)
+            coop.coop_release(ctx, got_c)
+            nxt += 0.005
+            time.sleep(max(0.0, nxt - time.perf_counter()))
+
+    th = threading.Thread(target=ticker)
+    t0 = time.perf_counter()
+    th.start()
+    runs = 0
+    while time.perf_counter() - t0 < 0.6:
+        run(False)
+        runs += 1
+    stream.synchronize()
+    stop.set()
+    th.join()
+    coop.coop_sync(ctx)
+    g = sorted(gat)
+    out["under_requests"] = {"runs": runs, "build_ms": round(0.6 / runs * 1e3, 3), "requests": len(g),
+                             "gather_ms_p50": round(g[len(g) // 2], 4), "gather_ms_p99": round(g[int(0.99 * (len(g) - 1))], 4)}
+    return out
+
+
 def batched(coop, ctx, dev, stream, flush, n_inst=64, seed=3, steps=5):
     """Batched form: 64 independent R-MAT instances (scales uniform in 12..20, edge factor
     16), a BFS and an SSSP job each, run as one autotuned, CUDA-graph-captured launch,
@@ -916,6 +984,7 @@ def secondary(coop, ctx, dev, stream, flush, args):
     out["preemption"] = preemption(coop, ctx, dev, stream)
     out["gather_by_kill_mode"] = gather_by_kill_mode(coop, ctx, dev, stream)
     out["topology_driven_sssp"] = topology_driven(coop, ctx, dev, stream, flush)
+    out["octree"] = octree(coop, ctx, dev, stream, flush)
     del ro, col, lv
     out["batched"] = batched(coop, ctx, dev, stream, flush)
     out["serving"] = serving(coop, dev)

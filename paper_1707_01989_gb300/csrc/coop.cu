@@ -1000,7 +1000,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) coop_octree_kernel(const __g
   (void)oct_reserve;
   __shared__ OctTask s_task;
   __shared__ int32_t s_state, s_workers_left;
-  __shared__ uint32_t s_slot, s_hist[8], s_off[8], s_cur[8];
+  __shared__ uint32_t s_slot, s_hist[8], s_off[8], s_cur[8], s_leafmask;
   OctCtl *c = p.ctl;
   const bool master = !join && blockIdx.x == 0;
   const unsigned tid = threadIdx.x, lane = tid & 31u;
@@ -1114,14 +1114,19 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) coop_octree_kernel(const __g
         if (bad) oct_error(p, ERR_GRAPH);
         workers_sync<NW>();
         if (tid == 0) {
-          uint32_t acc = 0u;
+          // children that will be leaves are emitted here, not queued: their points go
+          // straight to perm during the scatter and their records are written below
+          uint32_t acc = 0u, lm = 0u;
           for (int k = 0; k < 8; ++k) {
             s_off[k] = acc;
             s_cur[k] = acc;
             acc += s_hist[k];
+            if (s_hist[k] && (s_hist[k] <= p.leaf_cap || d + 1u >= p.max_depth)) lm |= 1u << k;
           }
+          s_leafmask = lm;
         }
         workers_sync<NW>();
+        const uint32_t leafmask = s_leafmask;
         const unsigned lt = lanemask_lt();
         for (uint32_t i0 = 0; i0 < t.count; i0 += T) {
           const uint32_t i = i0 + tid;
@@ -1147,10 +1152,14 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) coop_octree_kernel(const __g
           }
           if (i < t.count) {
             const uint32_t at = t.begin + pos;
-            p.bx[dst][at] = x;
-            p.by[dst][at] = y;
-            p.bz[dst][at] = z;
-            p.bi[dst][at] = id;
+            if ((leafmask >> o) & 1u) {
+              p.perm[at] = id;
+            } else {
+              p.bx[dst][at] = x;
+              p.by[dst][at] = y;
+              p.bz[dst][at] = z;
+              p.bi[dst][at] = id;
+            }
           }
         }
       }
@@ -1160,8 +1169,25 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) coop_octree_kernel(const __g
         OctTask ch[8];
         uint32_t nc = 0u;
         if (s_hist[0] != 0xFFFFFFFFu) {
+          const uint32_t lm = s_leafmask;
+          const uint32_t nleaf = (uint32_t)__popc(lm);
+          if (nleaf) {
+            const uint32_t li = atomicAdd(&c->leaves.v, nleaf);
+            uint32_t j = 0u;
+            for (uint32_t k = 0; k < 8u; ++k) {
+              if (!((lm >> k) & 1u)) continue;
+              if (li + j < p.max_leaves) {
+                p.leaf_code[li + j] = (t.code << 3) | k;
+                p.leaf_begin[li + j] = t.begin + s_off[k];
+                p.leaf_count[li + j] = s_hist[k];
+              } else {
+                oct_error(p, ERR_OVERFLOW);
+              }
+              ++j;
+            }
+          }
           for (uint32_t k = 0; k < 8u; ++k)
-            if (s_hist[k]) ch[nc++] = OctTask{t.begin + s_off[k], s_hist[k], (t.code << 3) | k};
+            if (s_hist[k] && !((lm >> k) & 1u)) ch[nc++] = OctTask{t.begin + s_off[k], s_hist[k], (t.code << 3) | k};
           atomicAdd(&c->moved, (unsigned long long)t.count);
         }
         bool ok = true;
