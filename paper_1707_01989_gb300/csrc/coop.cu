@@ -235,6 +235,30 @@ __device__ __forceinline__ void issue_groups(const Params &p, const uint32_t *qo
                                              const uint32_t *qv, uint32_t F, uint32_t Etot, uint32_t c,
                                              uint32_t E1, Window &w, uint32_t &wb, Landing<MODE> &pf, int sb,
                                              unsigned lane, unsigned lm_le) {
+  // Fast path: lane 0 holds the entry containing edge c - 32 (or c itself); if that entry
+  // also covers all of [c, c + 32 kUnroll) -- most iterations on wide R-MAT levels, whose
+  // rows run to hundreds of edges -- the positions are contiguous and the window stays.
+  const uint32_t end0 = __shfl_sync(kFull, w.end, 0);
+  if (end0 >= c + 32u * kUnroll) {
+    const uint32_t s0 = __shfl_sync(kFull, w.start, 0);
+    const uint32_t o0 = __shfl_sync(kFull, w.off, 0);
+    uint32_t du = 0u;
+    if (MODE == MODE_SSSP) du = __shfl_sync(kFull, w.du, 0);
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint32_t e = c + 32u * (uint32_t)u + lane;
+      if (e < E1) {
+        const uint32_t pos = s0 + (e - o0);
+        cp_async4(&pf.col[sb][u][lane], p.col + pos);
+        if constexpr (MODE == MODE_SSSP) {
+          cp_async4(&pf.w[sb][u][lane], p.w + pos);
+          pf.du[sb][u][lane] = du;
+        }
+      }
+    }
+    cp_async_commit();
+    return;
+  }
 #pragma unroll
   for (int u = 0; u < kUnroll; ++u) {
     const uint32_t cu = c + 32u * (uint32_t)u;

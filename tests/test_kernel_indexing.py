@@ -7,7 +7,9 @@ entries at that slot and maps each lane to one edge with a ballot over ended ent
 a __reduce_or of start bits and a popc over lanemask_le.  This test replays exactly
 that arithmetic in numpy (one vector = one warp) over random frontiers and checks that
 every lane reads column start[u] + (e - off[u]) of the entry u that owns edge e, i.e.
-that no column read can leave its row, and that every edge is expanded exactly once.
+that no column read can leave its row, and that every edge is expanded exactly once --
+including the fast path that skips the per-group arithmetic when lane 0's entry covers a
+whole 128-edge iteration.
 It runs before any GPU code does.
 """
 import numpy as np
@@ -75,28 +77,32 @@ def emulate_warp(qo, qs, F, Etot, E0, E1, wb=None):
         n = popc(ended)
         wb += n
         win = [win[(l + n) & 31] if l + n < 32 else load(qo, qs, F, Etot, wb + l) for l in range(32)]
-    c = E0
-    while c < E1:
-        ended = ballot(np.array([w[1] <= c for w in win]))
-        if ended:
-            n = popc(ended)
-            wb += n
-            new = []
-            for l in range(32):
-                new.append(win[(l + n) & 31] if l + n < 32 else load(qo, qs, F, Etot, wb + l))
-            win = new
-        bits = 0
-        for l in range(32):
-            rel = (win[l][0] - c) & FULL
-            if l != 0 and rel < 32:
-                bits |= 1 << rel
-        for l in range(32):
-            idx = popc(bits & ((2 << l) - 1))
-            s0, o0 = win[idx][2], win[idx][0]
-            e = c + l
-            if e < E1:
+    for it in range(E0, E1, 128):  # one kernel iteration: 4 groups of 32 edges
+        if win[0][1] >= it + 128:  # fast path: lane 0's entry covers the whole iteration
+            s0, o0 = win[0][2], win[0][0]
+            for e in range(it, min(it + 128, E1)):
                 out.append((e, (s0 + ((e - o0) & FULL)) & FULL))
-        c += 32
+            continue
+        for c in range(it, min(it + 128, E1), 32):
+            ended = ballot(np.array([w[1] <= c for w in win]))
+            if ended:
+                n = popc(ended)
+                wb += n
+                new = []
+                for l in range(32):
+                    new.append(win[(l + n) & 31] if l + n < 32 else load(qo, qs, F, Etot, wb + l))
+                win = new
+            bits = 0
+            for l in range(32):
+                rel = (win[l][0] - c) & FULL
+                if l != 0 and rel < 32:
+                    bits |= 1 << rel
+            for l in range(32):
+                idx = popc(bits & ((2 << l) - 1))
+                s0, o0 = win[idx][2], win[idx][0]
+                e = c + l
+                if e < E1:
+                    out.append((e, (s0 + ((e - o0) & FULL)) & FULL))
     return out
 
 
