@@ -923,7 +923,15 @@ struct OctParams {
   uint32_t n, leaf_cap, max_depth;
   uint32_t launched, kill_base, fork_base, coop;
   uint64_t timeout_ns;
+  uint32_t pre;  // 1: the top kPreDepth levels are partitioned grid-wide before the work stealing
+  uint32_t *cell_count, *cell_begin, *cell_cursor, *cell_leaf;  // kPreCells each
 };
+
+// Grid-wide partition of the top levels: the first kPreDepth levels of a large tree would
+// otherwise be partitioned by one CTA at a time (the root's n points by a single CTA).
+constexpr uint32_t kPreDepth = 3;
+constexpr uint32_t kPreCells = 1u << (3 * kPreDepth);  // 512 cells at depth 3
+constexpr uint32_t kPreMinPoints = 65536;
 
 __device__ __forceinline__ void oct_error(const OctParams &p, int code) {
   atomicCAS(&p.ctl->err.v, 0u, (uint32_t)code);
@@ -1231,11 +1239,15 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) coop_octree_kernel(const __g
 
 __global__ void __launch_bounds__(512) coop_octree_init(const __grid_constant__ OctParams p) {
   const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (size_t)gridDim.x * blockDim.x;
-  for (size_t i = tid; i < p.n; i += nth) {
-    p.bx[0][i] = p.x[i];
-    p.by[0][i] = p.y[i];
-    p.bz[0][i] = p.z[i];
-    p.bi[0][i] = (uint32_t)i;
+  if (p.pre) {
+    for (size_t i = tid; i < kPreCells; i += nth) p.cell_count[i] = 0u;
+  } else {
+    for (size_t i = tid; i < p.n; i += nth) {
+      p.bx[0][i] = p.x[i];
+      p.by[0][i] = p.y[i];
+      p.bz[0][i] = p.z[i];
+      p.bi[0][i] = (uint32_t)i;
+    }
   }
   if (tid == 0) {
     uint32_t *cw = reinterpret_cast<uint32_t *>(p.ctl);
@@ -1245,11 +1257,133 @@ __global__ void __launch_bounds__(512) coop_octree_init(const __grid_constant__ 
       p.queues[q].head = 0u;
       p.queues[q].tail = 0u;
     }
-    p.tasks[0] = OctTask{0u, p.n, 1ull};  // the root cell, in queue 0
-    p.queues[0].tail = 1u;
-    p.ctl->outstanding.v = 1u;
+    if (!p.pre) {
+      p.tasks[0] = OctTask{0u, p.n, 1ull};  // the root cell, in queue 0
+      p.queues[0].tail = 1u;
+      p.ctl->outstanding.v = 1u;
+    }
     p.ctl->launched.v = p.launched;
     *p.n_leaves = 0;
+  }
+}
+
+__device__ __forceinline__ uint32_t pre_cell(uint32_t x, uint32_t y, uint32_t z) {
+  uint32_t c = 0u;
+#pragma unroll
+  for (uint32_t d = 0; d < kPreDepth; ++d) c = (c << 3) | octant(x, y, z, 20u - d);
+  return c;
+}
+
+// Top levels, step 1: points per depth-3 cell (a shared-memory histogram per block).
+__global__ void __launch_bounds__(512) coop_octree_pre_hist(const __grid_constant__ OctParams p) {
+  __shared__ uint32_t h[kPreCells];
+  for (uint32_t i = threadIdx.x; i < kPreCells; i += blockDim.x) h[i] = 0u;
+  __syncthreads();
+  bool bad = false;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t x = p.x[i], y = p.y[i], z = p.z[i];
+    if ((x | y | z) >> 21) bad = true;
+    atomicAdd(&h[pre_cell(x, y, z)], 1u);
+  }
+  if (bad) oct_error(p, ERR_GRAPH);
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < kPreCells; i += blockDim.x)
+    if (h[i]) atomicAdd(&p.cell_count[i], h[i]);
+}
+
+// Top levels, step 2 (one block): the cells' ranges in octant order (so every cell above
+// depth 3 is contiguous), the leaves above depth 3 -- recorded here, their points go to
+// perm in step 3 -- and one task per non-empty depth-3 cell below no leaf, spread over the
+// queues.  The tree is the one a root task would have produced.
+__global__ void __launch_bounds__(kPreCells) coop_octree_pre_plan(const __grid_constant__ OctParams p) {
+  __shared__ uint32_t cnt[kPreCells], beg[kPreCells], n2[64], n1[8];
+  __shared__ uint32_t s_tasks;
+  const uint32_t t = threadIdx.x;
+  cnt[t] = p.cell_count[t];
+  if (t == 0) s_tasks = 0u;
+  __syncthreads();
+  if (t < 64) {
+    uint32_t a = 0u;
+    for (int k = 0; k < 8; ++k) a += cnt[t * 8 + k];
+    n2[t] = a;
+  }
+  if (t == 0) {  // exclusive prefix over the 512 cells, in octant order
+    uint32_t acc = 0u;
+    for (uint32_t i = 0; i < kPreCells; ++i) {
+      beg[i] = acc;
+      acc += cnt[i];
+    }
+  }
+  __syncthreads();
+  if (t < 8) {
+    uint32_t a = 0u;
+    for (int k = 0; k < 8; ++k) a += n2[t * 8 + k];
+    n1[t] = a;
+  }
+  __syncthreads();
+  // which level, if any, ends this cell's branch above depth 3 (the root always splits:
+  // this path runs only for n > leaf_cap and max_depth >= 3)
+  const uint32_t d0 = t >> 6, d01 = t >> 3;
+  uint32_t leaf_depth = 0u;  // 0: none, the depth-3 cell is a task
+  if (n1[d0] <= p.leaf_cap || p.max_depth <= 1u) leaf_depth = 1u;
+  else if (n2[d01] <= p.leaf_cap || p.max_depth <= 2u) leaf_depth = 2u;
+  p.cell_leaf[t] = leaf_depth;
+  p.cell_begin[t] = beg[t];
+  p.cell_cursor[t] = beg[t];
+  // one record per leaf, written by the leaf's first cell
+  const bool first1 = (t & 63u) == 0u, first2 = (t & 7u) == 0u;
+  if ((leaf_depth == 1u && first1 && n1[d0]) || (leaf_depth == 2u && first2 && n2[d01])) {
+    const uint32_t li = atomicAdd(&p.ctl->leaves.v, 1u);
+    const unsigned long long code = leaf_depth == 1u ? (8ull | d0) : (64ull | d01);
+    if (li < p.max_leaves) {
+      p.leaf_code[li] = code;
+      p.leaf_begin[li] = beg[t];
+      p.leaf_count[li] = leaf_depth == 1u ? n1[d0] : n2[d01];
+    } else {
+      oct_error(p, ERR_OVERFLOW);
+    }
+  }
+  if (leaf_depth == 0u && cnt[t]) {
+    // over the queues of the launched CTAs only: a CTA looks at the queue slots taken so
+    // far, and the main grid's CTAs take the first min(launched, kOctQueues)
+    const uint32_t k = atomicAdd(&s_tasks, 1u);
+    const uint32_t nq = min(p.launched, kOctQueues);
+    const uint32_t q = k % nq, at = k / nq;  // at <= 511 < kOctQueueCap
+    p.tasks[(size_t)q * kOctQueueCap + at] = OctTask{beg[t], cnt[t], 512ull | t};
+    atomicAdd(&p.queues[q].tail, 1u);
+  }
+  __syncthreads();
+  if (t == 0) p.ctl->outstanding.v = s_tasks;
+}
+
+// Top levels, step 3: every point to its depth-3 cell (buffer 1, as the depth-3 tasks read
+// it) or, below a leaf, straight to perm.  Each block reserves its points' places per cell
+// with one atomic, then ranks them in shared memory.
+__global__ void __launch_bounds__(512) coop_octree_pre_scatter(const __grid_constant__ OctParams p) {
+  __shared__ uint32_t h[kPreCells], base[kPreCells];
+  const size_t per = (p.n + gridDim.x - 1) / gridDim.x;
+  const size_t lo = (size_t)blockIdx.x * per, hi = min((size_t)p.n, lo + per);
+  for (uint32_t i = threadIdx.x; i < kPreCells; i += blockDim.x) h[i] = 0u;
+  __syncthreads();
+  for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&h[pre_cell(p.x[i], p.y[i], p.z[i])], 1u);
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < kPreCells; i += blockDim.x) {
+    base[i] = h[i] ? atomicAdd(&p.cell_cursor[i], h[i]) : 0u;
+    h[i] = 0u;
+  }
+  __syncthreads();
+  for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const uint32_t x = p.x[i], y = p.y[i], z = p.z[i];
+    const uint32_t c = pre_cell(x, y, z);
+    const uint32_t at = base[c] + atomicAdd(&h[c], 1u);
+    if (p.cell_leaf[c]) {
+      p.perm[at] = (uint32_t)i;
+    } else {
+      p.bx[1][at] = x;
+      p.by[1][at] = y;
+      p.bz[1][at] = z;
+      p.bi[1][at] = (uint32_t)i;
+    }
   }
 }
 
@@ -1575,6 +1709,8 @@ coop_status coop_init(int device, int max_ctas, int threads_per_cta, coop_ctx **
     const void *all[] = {traverse_fn<MODE_BFS>(nw), traverse_fn<MODE_SSSP>(nw), traverse_fn<MODE_BARRIER>(nw),
                          traverse_fn<MODE_PSSSP>(nw), (const void *)coop_init_kernel<MODE_PSSSP>, octree_fn(nw),
                          (const void *)coop_octree_init, (const void *)coop_octree_finish,
+                         (const void *)coop_octree_pre_hist, (const void *)coop_octree_pre_plan,
+                         (const void *)coop_octree_pre_scatter,
                          (const void *)coop_init_kernel<MODE_BFS>, (const void *)coop_init_kernel<MODE_SSSP>,
                          (const void *)coop_init_kernel<MODE_BARRIER>, (const void *)coop_saxpy_kernel};
     for (const void *k : all) {
@@ -2665,7 +2801,7 @@ coop_status ensure_oct_scratch(coop_ctx *c, int64_t n) {
   const int64_t cap = std::max<int64_t>(n, 1024);
   const size_t words = ((size_t)cap * 4 + 255) & ~(size_t)255;
   const size_t total = 8 * words + sizeof(OctQueue) * kOctQueues + sizeof(OctTask) * kOctQueues * kOctQueueCap +
-                       sizeof(OctCtl) + 1024;
+                       sizeof(OctCtl) + 4 * kPreCells * sizeof(uint32_t) + 1024;
   if (cudaMalloc(&c->oct_scratch, total) != cudaSuccess) {
     (void)cudaGetLastError();
     c->oct_scratch = nullptr;
@@ -2715,6 +2851,12 @@ coop_status coop_octree(coop_ctx *c, const uint32_t *d_x, const uint32_t *d_y, c
     p.tasks = reinterpret_cast<OctTask *>(at);
     at += sizeof(OctTask) * kOctQueues * kOctQueueCap;
     p.ctl = reinterpret_cast<OctCtl *>(((uintptr_t)at + 127) & ~(uintptr_t)127);
+    uint32_t *cells = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(p.ctl) + sizeof(OctCtl));
+    p.cell_count = cells;
+    p.cell_begin = cells + kPreCells;
+    p.cell_cursor = cells + 2 * kPreCells;
+    p.cell_leaf = cells + 3 * kPreCells;
+    p.pre = ((uint32_t)n >= kPreMinPoints && (uint32_t)max_depth >= kPreDepth && n > leaf_cap) ? 1u : 0u;
     for (int b = 0; b < 2; ++b) {
       p.bx[b] = w[4 * b];
       p.by[b] = w[4 * b + 1];
@@ -2746,6 +2888,11 @@ coop_status coop_octree(coop_ctx *c, const uint32_t *d_x, const uint32_t *d_y, c
     store_release(&c->mbox->fork_req, c->fork_req);
     coop_octree_init<<<c->sm_count * 4, 512, 0, s>>>(p);
     if (c->timing) cudaEventRecord(c->ev_t0, s);
+    if (p.pre) {
+      coop_octree_pre_hist<<<c->sm_count * 4, 512, 0, s>>>(p);
+      coop_octree_pre_plan<<<1, kPreCells, 0, s>>>(p);
+      coop_octree_pre_scatter<<<c->sm_count * 4, 512, 0, s>>>(p);
+    }
     switch (c->nw) {
       case 31: coop_octree_kernel<31><<<p.launched, 32 * 32, kTraverseSmemMin, s>>>(p, 0); break;
       case 23: coop_octree_kernel<23><<<p.launched, 24 * 32, kTraverseSmemMin, s>>>(p, 0); break;

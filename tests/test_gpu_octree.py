@@ -58,7 +58,11 @@ def _check(pts, cap, md, res):
 @pytest.mark.parametrize("kind,n,cap,md", [("uniform", 50000, 32, 21), ("clustered", 120000, 16, 21),
                                            ("clustered", 30000, 1, 21), ("uniform", 20000, 8, 3),
                                            ("clustered", 5000, 64, 0), ("uniform", 1, 4, 21),
-                                           ("clustered", 700, 1000, 21)])
+                                           ("clustered", 700, 1000, 21),
+                                           # large inputs take the grid-wide partition of the top
+                                           # levels: leaves above depth 3, and max_depth exactly 3
+                                           ("clustered", 100000, 3000, 21), ("uniform", 70000, 8, 3),
+                                           ("clustered", 300000, 32, 21)])
 def test_octree_matches_oracle(ctx, kind, n, cap, md):
     pts = gg.points(n, 70 + n % 97, kind)
     _check(pts, cap, md, _run(ctx, pts, cap, md))
