@@ -48,8 +48,8 @@ WORKLOADS = {
 # workload, from the ncu captures summarised in profiles/; an entry is used only while
 # the kernel sources still have the digest it was taken on (otherwise null).
 TRAFFIC = {
-    "rmat20-sssp": {"sources_sha": "6e31aa8f62aad3c7", "bytes": 374778112},
-    "rmat22-bfs": {"sources_sha": "6e31aa8f62aad3c7", "bytes": 391689472},
+    "rmat20-sssp": {"sources_sha": "f094b2d5c594449b", "bytes": 377287680},
+    "rmat22-bfs": {"sources_sha": "f094b2d5c594449b", "bytes": 390945792},
 }
 
 
