@@ -12,8 +12,11 @@ Also on the same JSON line: the roofline of the persistent kernel (algorithmic b
 copy bandwidth), the end-to-end number through the C ABI with host buffers (H2D of
 the CSR and weights, D2H of the distances inside the timed region), the CPU oracle
 timed on this host, clock samples taken during the timed region, and secondary
-figures: BFS on R-MAT scale 22, the 256x256 grid BFS (barrier-latency bound) and the
-non-cooperative baseline's overhead ratio.
+figures (skipped with --no-extras): BFS on R-MAT scale 22 with the non-cooperative
+baseline's overhead ratio and random kill/fork schedules, the co-runner (fp32 saxpy on
+half the SMs every 16.7 ms) with and without cooperation, gather time under each kill
+mode, the topology-driven SSSP, the work-stealing octree, the batched and served forms,
+the 256x256 grid BFS (barrier-latency bound) and empty-barrier latency.
 
 --impl reference times the CPU oracle (binary-heap Dijkstra, one core) on the same
 workload: the slow reference arm.

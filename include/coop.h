@@ -11,6 +11,14 @@
  * (coop_request_resources) and new CTAs join through request_fork when the host
  * returns them (coop_release).  Results do not depend on the schedule.
  *
+ * Entry points: frontier traversals (coop_bfs, coop_sssp; their non-cooperative
+ * baselines), the topology-driven SSSP of Table 1's p-sssp (coop_sssp_topo), the
+ * work-stealing octree of Table 1 (coop_octree), many traversals in one persistent
+ * launch (coop_batch_*), a request loop with continuous batching (coop_server_*), the
+ * co-running task (coop_saxpy), and the place where host requests are served
+ * (coop_set_kill_mode: regular barrier, query barrier, or query barrier plus kill points
+ * between chunks).
+ *
  * Conventions
  *  - Every pointer argument named d_* or inside coop_csr is DEVICE memory owned by the
  *    caller (e.g. a torch tensor); it must stay valid until the traversal's stream
@@ -52,8 +60,9 @@ typedef enum {
     COOP_ECUDA = -3,     /* a CUDA runtime call failed */
     COOP_ETIMEOUT = -4,  /* a device wait or a host gather exceeded its time limit */
     COOP_EBUSY = -5,     /* the context is busy (e.g. destroy with a traversal in flight) */
-    COOP_EOVERFLOW = -6, /* an SSSP distance did not fit below 2^32 - 1 */
-    COOP_EGRAPH = -7     /* malformed CSR detected on the device (id or offset out of range) */
+    COOP_EOVERFLOW = -6, /* an SSSP distance did not fit below 2^32 - 1; octree: out of leaf or queue room */
+    COOP_EGRAPH = -7     /* malformed CSR detected on the device (id or offset out of range); octree: a
+                            coordinate at or above 2^21 */
 } coop_status;
 
 /* A directed graph in int32 CSR form; row_off and col are device pointers. */

@@ -1,26 +1,34 @@
-// coop.cu - cooperative BFS / SSSP kernels for GB300 (sm_103a) and the C ABI of libcoop.so.
+// coop.cu - cooperative kernels for GB300 (sm_103a) and the C ABI of libcoop.so.
 //
-// One traversal = one init kernel + one persistent kernel (+ fork launches on the
-// context's join stream).  Inside the persistent kernel each interval between two
-// resizing barriers expands one frontier (Fig. 4 of "Cooperative Kernels", Sec. 3.2):
+// One traversal = one init kernel + one persistent kernel (+ CTAs the kernel itself
+// launches from the device when it grows).  Inside the persistent kernel each interval
+// between two resizing barriers expands one frontier (Fig. 4 of "Cooperative Kernels",
+// Sec. 3.2):
 //
 //  * the frontier lives in a queue of (first column, edge-space offset[, vertex]) entries;
 //    the offsets are the exclusive prefix sums of the frontier's out-degrees, built on
 //    the fly by the warp-aggregated enqueue (one 64-bit atomic per warp adds both the
-//    vertex count and the edge count);
-//  * the interval's edge space [0, edges) is split evenly over the M * 32 worker warps of
-//    the active CTAs by logical id -- the paper's tid / stride re-partition, recomputed
-//    after every resizing barrier, applied to edges instead of vertices so that skewed
-//    degrees (R-MAT hubs) are balanced;
-//  * a warp walks its edge range 32 consecutive edges at a time: a window of 32 frontier
-//    entries sits in registers, a ballot finds the entries that ended, one __reduce_or
-//    marks the entries that start inside the chunk, and a popc over lanemask_le gives
-//    each lane its source entry, so column loads are coalesced;
+//    vertex count and the edge count), which also writes a chunk index (the entry holding
+//    every 128th edge);
+//  * the interval's edge space [0, edges) is cut into chunks of 32-edge units; a warp's
+//    first chunk follows from its logical id -- the paper's tid / stride re-partition,
+//    recomputed after every resizing barrier, applied to edges instead of vertices so that
+//    skewed degrees (R-MAT hubs) are balanced -- and further chunks come from a shared
+//    cursor; the claim of the next chunk is also the expansion's offer_kill point;
+//  * a warp walks a chunk 128 edges (4 groups of 32) per iteration: a window of 32
+//    frontier entries sits in registers, a ballot finds the entries that ended, one
+//    __reduce_or marks the entries that start inside a group, and a popc over lanemask_le
+//    gives each lane its source entry; the columns (and weights) of the next iteration
+//    are copied into a shared-memory landing slot with cp.async while the current one is
+//    claimed;
 //  * BFS claims a vertex with an atomicOr on a 1-bit-per-vertex visited bitmap (checked
 //    first with a plain load; stale reads only cost an extra atomic), writes its level
 //    and enqueues it if its out-degree is non-zero; SSSP keeps (distance, round stamp)
 //    of a vertex in one 64-bit word, so a single 64-bit atomicMin both lowers the
 //    distance and tells whether the vertex is already queued for the next round.
+//
+// Also here: the topology-driven SSSP (Table 1 p-sssp), the work-stealing octree (Table 1
+// octree), the batched launch, the serving loop, the co-runner and the allocation-free BFS.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>

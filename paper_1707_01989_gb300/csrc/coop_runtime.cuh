@@ -24,9 +24,13 @@
 //    the releaser before the release and read by every CTA after it; joiners read the
 //    same record, which is "thread 0 of workgroup 0's" transmitted state since those
 //    values are uniform across the kernel (the observation of Appendix B).
-//  * the scheduler side of query(): a scheduler warp in the master CTA mirrors the host's
-//    request counter (mapped pinned memory, system scope) into device memory, so the
-//    barrier's release path reads only L2, and launches the CTAs the host gives back.
+//  * the scheduler side of query(): a scheduler warp in the master CTA turns the host's
+//    request counter (mapped pinned memory, system scope) into an epoch-stamped kill
+//    target in L2 -- CTAs with logical ids at or above it leave at their next offer_kill
+//    point, and the releaser closes it for the interval -- so the release path reads only
+//    L2; it also launches the CTAs the host gives back.  Where requests are served is a
+//    per-context mode (KillMode): the regular barrier of Sec. 4.2, the query barrier, or
+//    the query barrier plus a kill point between chunks of an interval.
 //
 // Every spin-wait reads %globaltimer and gives up after the context's limit, setting a
 // sticky error that all other waits observe; nothing here can wait forever.
