@@ -102,3 +102,40 @@ def test_batch_tune(ctx, cuda_device):
     coop.coop_batch_run(b, use_graph=True)
     _check(expect)
     coop.coop_batch_destroy(b)
+
+
+@pytest.mark.slow
+def test_batch_full_configuration(ctx, cuda_device):
+    """The batched workload at its full size: 64 R-MAT instances, scales uniform in
+    12..20 (seed 3, instance graphs seeded 1000 + i, weights 2000 + i), a BFS and an
+    SSSP job each, blocks chosen by the autotuner, run from the captured CUDA graph;
+    all 128 outputs against the oracle."""
+    import torch
+    rng = np.random.default_rng(3)
+    scales = rng.integers(12, 21, size=64)
+    jobs, keep, expect = [], [], []
+    for i, sc in enumerate(scales):
+        g = gg.rmat(int(sc), 16, seed=1000 + i)
+        w = gg.weights(g, 2000 + i)
+        src = gg.max_out_degree_vertex(g)
+        dg = DevGraph(g, w)
+        lv, dist = dg.empty(), dg.empty()
+        keep += [dg, lv, dist]
+        jobs += [coop.make_job(dg.csr, src, lv), coop.make_job(dg.csr, src, dist, dg.w)]
+        expect += [(lv, (g, src), "bfs"), (dist, (g, w, src), "sssp")]
+    b = coop.coop_batch_create(ctx, jobs, keep)
+    try:
+        coop.coop_batch_tune(b)
+        for out, _, _ in expect:
+            out.fill_(0x5A5A5A5A)
+        coop.coop_batch_run(b, use_graph=True)
+        coop.coop_batch_run(b, use_graph=True)
+        torch.cuda.synchronize()
+        for i, (out, args, kind) in enumerate(expect):
+            got = out.cpu().numpy()
+            if kind == "bfs":
+                assert_same(got, oracle.bfs(*args), f"job {i} (bfs, scale {scales[i // 2]})")
+            else:
+                assert_same(got.view(np.uint32), oracle.dijkstra(*args), f"job {i} (sssp, scale {scales[i // 2]})")
+    finally:
+        coop.coop_batch_destroy(b)

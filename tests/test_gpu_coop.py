@@ -304,3 +304,19 @@ def test_topology_driven_sssp_under_schedules(ctx, seed):
     assert_same(out.cpu().numpy().view(np.uint32), oracle.dijkstra(g, w, src), f"p-sssp schedule {seed}")
     assert st.kills > 0 or st.forks > 0
     _replay(ctx, st)
+
+
+@pytest.mark.slow
+def test_full_size_rmat22_bfs_under_a_schedule(ctx):
+    """R-MAT scale 22 BFS (the cooperative-multitasking workload) under a forced random
+    kill/fork schedule: bit-exact levels and a legal resize log."""
+    g = gg.rmat(22, 16, seed=22)
+    src = gg.max_out_degree_vertex(g)
+    coop.coop_set_schedule(ctx, 3, p_kill=0.3, p_fork=0.5)  # the bench's seed 3: kills and forks
+    try:
+        lv, st = run_bfs(ctx, DevGraph(g), src)
+    finally:
+        coop.coop_set_schedule(ctx, 0, 0.0, 0.0)
+    assert_same(lv, oracle.bfs(g, src), "rmat22 bfs under a schedule")
+    assert st.kills > 0 and st.forks > 0
+    _replay(ctx, st)
