@@ -134,3 +134,10 @@ def test_octree_errors(ctx):
     assert len(codes) == 0
     # the context still works
     _check(pts, 8, 21, _run(ctx, pts, 8, 21))
+
+
+@pytest.mark.slow
+def test_octree_full_size(ctx):
+    """4M clustered points, leaf_cap 32: the benchmark's octree, every point's leaf checked."""
+    pts = gg.points(1 << 22, 90, "clustered")
+    _check(pts, 32, 21, _run(ctx, pts, 32, 21))

@@ -101,3 +101,47 @@ def test_server_budget_and_arguments(cuda_device):
     assert r.status == 0 and r.latency_us > 0
     assert_same(out.cpu().numpy(), oracle.bfs(g, 0), "single served query")
     coop.coop_server_destroy(sv)
+
+
+@pytest.mark.slow
+def test_serving_full_graph_set(cuda_device):
+    """The serving workload's graph set at full size: 32 device-resident R-MAT graphs of
+    scales 14..21 (seeded as in the benchmark), 4 slots under a 60 GB budget; 40 BFS /
+    SSSP queries with random sources submitted in bursts so that they overlap and running
+    queries are resized; every result against the oracle."""
+    import torch
+    rng_g, rng_s = np.random.default_rng(4), np.random.default_rng(16)
+    scales = rng_g.integers(14, 22, size=32)
+    sv = coop.coop_server_create(0, slots=4, hbm_budget_bytes=60 << 30)
+    graphs = []
+    for i, sc in enumerate(scales):
+        g = gg.rmat(int(sc), 16, seed=3000 + i)
+        w = gg.weights(g, 4000 + i)
+        dg = DevGraph(g, w)
+        coop.coop_server_add_graph(sv, dg.csr, dg.w, keep=(dg,))
+        graphs.append((g, w, dg))
+    queries = []
+    for k in range(40):
+        gi = int(rng_s.integers(0, 32))
+        kind = coop.COOP_JOB_BFS if k % 2 else coop.COOP_JOB_SSSP
+        src = int(rng_s.integers(0, graphs[gi][0].num_vertices))
+        out = graphs[gi][2].empty()
+        out.fill_(0x5A5A5A5A)
+        queries.append((gi, kind, src, out))
+    tickets = []
+    for k, (gi, kind, src, out) in enumerate(queries):
+        tickets.append(coop.coop_server_submit(sv, gi, kind, src, out))
+        if k % 8 == 7:
+            time.sleep(0.002)
+    results = [coop.coop_server_wait(sv, t, timeout_us=30_000_000) for t in tickets]
+    coop.coop_server_destroy(sv)
+    assert all(r.status == coop.COOP_OK for r in results)
+    assert any(r.ctas < coop.coop_query(coop.coop_init(0))["max_ctas"] for r in results)
+    torch.cuda.synchronize()
+    for (gi, kind, src, out), r in zip(queries, results):
+        g, w, _ = graphs[gi]
+        got = out.cpu().numpy()
+        if kind == coop.COOP_JOB_BFS:
+            assert_same(got, oracle.bfs(g, src), f"bfs on graph {gi} (scale {scales[gi]}) from {src}")
+        else:
+            assert_same(got.view(np.uint32), oracle.dijkstra(g, w, src), f"sssp on graph {gi} from {src}")

@@ -242,3 +242,13 @@ def test_topology_driven_sssp_overflow_reported(ctx):
     w = np.array([0xFFFFFFF0, 0xFFFFFFF0, 1], dtype=np.uint32)
     d, st = _run_topo(ctx, DevGraph(g, w), 0, ok=(coop.COOP_EOVERFLOW,))
     assert st.status == coop.COOP_EOVERFLOW
+
+
+@pytest.mark.slow
+def test_full_size_rmat20_topology_driven_sssp(ctx):
+    g = gg.rmat(20, 16, seed=20)
+    w = gg.weights(g, 21)
+    src = gg.max_out_degree_vertex(g)
+    d, st = _run_topo(ctx, DevGraph(g, w), src)
+    assert_same(d, oracle.dijkstra(g, w, src), "rmat20 p-sssp")
+    assert st.barriers % 3 == 0
