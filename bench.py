@@ -403,7 +403,7 @@ def random_schedules(coop, ctx, csr, src, lv, ref, stream, es, seeds=(0, 1, 2, 3
     return res
 
 
-def corunner(coop, ctx, dev, csr, src, lv, stream, period_s=1.0 / 60.0, duration_s=1.5):
+def corunner(coop, ctx, dev, csr, src, lv, stream, period_s=1.0 / 60.0, duration_s=1.5, work=None):
     """Cooperative multitasking: a periodic fp32 saxpy over 64 MB (x and y, 16.7 ms period)
     that claims half the SMs from back-to-back R-MAT 22 BFS traversals.
 
@@ -480,7 +480,12 @@ def corunner(coop, ctx, dev, csr, src, lv, stream, period_s=1.0 / 60.0, duration
             "gather_ms_p50": pct(gat, 0.5), "gather_ms_p99": pct(gat, 0.99),
             "deadline_ms": 2.0, "deadline_met_frac": round(sum(l <= 2.0 for l in lat) / max(1, len(lat)), 4),
             "traversal_ms_alone": round(per_alone * 1e3, 4), "traversal_ms_corun": round(per_co * 1e3, 4),
-            "coop_slowdown": round(per_co / per_alone, 4)}
+            "coop_slowdown": round(per_co / per_alone, 4),
+            **({} if work is None else {
+                # host-timed back-to-back traversals (launch gaps included)
+                "gteps_alone": round(work[0] / per_alone / 1e9, 3), "gteps_corun": round(work[0] / per_co / 1e9, 3),
+                "hbm_frac_alone": round(work[1] / per_alone / 1e9 / work[2], 4),
+                "hbm_frac_corun": round(work[1] / per_co / 1e9 / work[2], 4)})}
 
 
 def preemption(coop, ctx, dev, stream, period_s=1.0 / 60.0, duration_s=1.0):
@@ -969,7 +974,7 @@ def secondary(coop, ctx, dev, stream, flush, args):
                          "hbm_frac": round(B / (kus / 1e6) / 1e9 / hbm, 4),
                          "baseline_kernel_us": round(kusb, 2), "coop_overhead": round(kus / kusb, 4)}
     out["bfs_rmat22_schedules"] = random_schedules(coop, ctx, csr, src, lv, lvh, stream, es)
-    out["corunner"] = corunner(coop, ctx, dev, csr, src, lv, stream)
+    out["corunner"] = corunner(coop, ctx, dev, csr, src, lv, stream, work=(es, B, hbm))
     del ro, col, lv
     # grid 256x256 BFS: barrier-latency bound
     g = gg.grid(256, 256)
