@@ -51,8 +51,8 @@ WORKLOADS = {
 # workload, from the ncu captures summarised in profiles/; an entry is used only while
 # the kernel sources still have the digest it was taken on (otherwise null).
 TRAFFIC = {
-    "rmat20-sssp": {"sources_sha": "f094b2d5c594449b", "bytes": 377287680},
-    "rmat22-bfs": {"sources_sha": "f094b2d5c594449b", "bytes": 390945792},
+    "rmat20-sssp": {"sources_sha": "4d552d6391af2f3c", "bytes": 373007872},
+    "rmat22-bfs": {"sources_sha": "4d552d6391af2f3c", "bytes": 392425728},
 }
 
 
