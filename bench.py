@@ -929,11 +929,30 @@ def serving(coop, dev, n_graphs=32, rate=200.0, duration_s=3.0, slots=4, budget=
 
 def secondary(coop, ctx, dev, stream, flush, args):
     """BFS on R-MAT 22, grid BFS, the co-runner with and without cooperation, batching,
-    serving, barrier latency and the non-cooperative baseline ratio."""
+    serving, barrier latency and the non-cooperative baseline ratio.  Each part runs on
+    its own: one that fails records its error under its key and the others still run."""
+    import traceback
     import numpy as np
     import torch
     import graphgen as gg
     out = {}
+
+    def guarded(name, fn, label=None):
+        try:
+            res = fn()
+            if isinstance(res, dict) and name is None:
+                out.update(res)
+            else:
+                out[name] = res
+        except Exception as exc:  # recorded, so that the JSON line is still printed
+            out[name or label] = {"error": f"{type(exc).__name__}: {exc}",
+                                    "where": traceback.format_exc(limit=3).splitlines()[-3:]}
+            try:
+                torch.cuda.synchronize(dev)
+                coop.coop_set_schedule(ctx, 0, 0.0, 0.0)
+                coop.coop_set_kill_mode(ctx, coop.COOP_KILL_CHUNK)
+            except Exception:
+                pass
 
     def timed(fn, reps):
         ts, ks = [], []
@@ -951,72 +970,82 @@ def secondary(coop, ctx, dev, stream, flush, args):
         return statistics.median(ts), statistics.median(ks)
 
     hbm, _ = peaks()
-    # BFS on R-MAT scale 22
-    g = gg.rmat(22, 16, seed=22)
-    src = gg.max_out_degree_vertex(g)
-    ro = torch.from_numpy(np.array(g.row_off)).to(dev)
-    col = torch.from_numpy(np.array(g.col)).to(dev)
-    lv = torch.empty(g.num_vertices, dtype=torch.int32, device=dev)
-    csr = coop.make_csr(ro, col)
-    f = lambda: coop.coop_bfs(ctx, csr, src, lv, stream=stream)
-    for _ in range(3):
-        f()
-    ms, kus = timed(f, max(3, args.steps))
-    lvh = lv.cpu().numpy()
-    vr, es = reached_work(g, lvh >= 0)
-    B = 4 * g.num_vertices + 20 * vr + 8 * es
-    fb = lambda: coop.coop_bfs_baseline(ctx, csr, src, lv, stream=stream)
-    for _ in range(2):
-        fb()
-    msb, kusb = timed(fb, max(3, args.steps))
-    out["bfs_rmat22"] = {"V": g.num_vertices, "E": g.num_edges, "E_s": es, "V_reached": vr,
-                         "ms": round(ms, 4), "kernel_us": round(kus, 2), "gteps": round(es / (ms / 1e3) / 1e9, 3),
-                         "hbm_frac": round(B / (kus / 1e6) / 1e9 / hbm, 4),
-                         "baseline_kernel_us": round(kusb, 2), "coop_overhead": round(kus / kusb, 4)}
-    out["bfs_rmat22_schedules"] = random_schedules(coop, ctx, csr, src, lv, lvh, stream, es)
-    out["corunner"] = corunner(coop, ctx, dev, csr, src, lv, stream, work=(es, B, hbm))
-    del ro, col, lv
-    # grid 256x256 BFS: barrier-latency bound
-    g = gg.grid(256, 256)
-    ro = torch.from_numpy(np.array(g.row_off)).to(dev)
-    col = torch.from_numpy(np.array(g.col)).to(dev)
-    lv = torch.empty(g.num_vertices, dtype=torch.int32, device=dev)
-    csr = coop.make_csr(ro, col)
-    f = lambda: coop.coop_bfs(ctx, csr, 0, lv, stream=stream)
-    for _ in range(3):
-        f()
-    ms, kus = timed(f, max(3, args.steps))
-    ok = bool(np.array_equal(lv.cpu().numpy(), np.add(*np.divmod(np.arange(65536), 256))))
-    out["grid_bfs"] = {"levels": 511, "ms": round(ms, 4), "kernel_us": round(kus, 2),
-                       "us_per_level": round(kus / 511, 3), "closed_form_ok": ok}
-    out["preemption"] = preemption(coop, ctx, dev, stream)
-    out["gather_by_kill_mode"] = gather_by_kill_mode(coop, ctx, dev, stream)
-    out["topology_driven_sssp"] = topology_driven(coop, ctx, dev, stream, flush)
-    out["octree"] = octree(coop, ctx, dev, stream, flush)
-    del ro, col, lv
-    out["batched"] = batched(coop, ctx, dev, stream, flush)
-    out["serving"] = serving(coop, dev)
-    # empty resizing barriers: at M = N, at M = N/2 (half the CTAs lent), and at M = N
-    # with a forced schedule that kills or forks at about one barrier in eight
-    n = 20000
-    N = coop.coop_query(ctx)["max_ctas"]
-    f = lambda: coop.coop_barrier_bench(ctx, n, stream=stream, stats=False)
 
-    def per_barrier():
-        f()
-        _, kus = timed(f, 3)
-        return round(kus / n, 4)
+    def rmat22():
+        # BFS on R-MAT scale 22, its schedules and the co-runner on it
+        g = gg.rmat(22, 16, seed=22)
+        src = gg.max_out_degree_vertex(g)
+        ro = torch.from_numpy(np.array(g.row_off)).to(dev)
+        col = torch.from_numpy(np.array(g.col)).to(dev)
+        lv = torch.empty(g.num_vertices, dtype=torch.int32, device=dev)
+        csr = coop.make_csr(ro, col)
+        f = lambda: coop.coop_bfs(ctx, csr, src, lv, stream=stream)
+        for _ in range(3):
+            f()
+        ms, kus = timed(f, max(3, args.steps))
+        lvh = lv.cpu().numpy()
+        vr, es = reached_work(g, lvh >= 0)
+        B = 4 * g.num_vertices + 20 * vr + 8 * es
+        fb = lambda: coop.coop_bfs_baseline(ctx, csr, src, lv, stream=stream)
+        for _ in range(2):
+            fb()
+        msb, kusb = timed(fb, max(3, args.steps))
+        res = {"bfs_rmat22": {"V": g.num_vertices, "E": g.num_edges, "E_s": es, "V_reached": vr,
+                              "ms": round(ms, 4), "kernel_us": round(kus, 2),
+                              "gteps": round(es / (ms / 1e3) / 1e9, 3), "hbm_frac": round(B / (kus / 1e6) / 1e9 / hbm, 4),
+                              "baseline_kernel_us": round(kusb, 2), "coop_overhead": round(kus / kusb, 4)}}
+        res["bfs_rmat22_schedules"] = random_schedules(coop, ctx, csr, src, lv, lvh, stream, es)
+        res["corunner"] = corunner(coop, ctx, dev, csr, src, lv, stream, work=(es, B, hbm))
+        return res
 
-    out["barrier_us"] = per_barrier()
-    got = coop.coop_request_resources(ctx, N // 2)
-    out["barrier_us_half"] = per_barrier()
-    coop.coop_release(ctx, got)
-    coop.coop_set_schedule(ctx, 7, p_kill=1.0 / 16, p_fork=1.0 / 16)
-    us = per_barrier()
-    st = coop.coop_get_stats(ctx)
-    coop.coop_set_schedule(ctx, 0, 0.0, 0.0)
-    out["barrier_us_resizing"] = {"us": us, "kills": st.kills, "forks": st.forks, "barriers": st.barriers,
-                                  "min_active": st.min_active}
+    def grid():
+        # grid 256x256 BFS: barrier-latency bound
+        g = gg.grid(256, 256)
+        ro = torch.from_numpy(np.array(g.row_off)).to(dev)
+        col = torch.from_numpy(np.array(g.col)).to(dev)
+        lv = torch.empty(g.num_vertices, dtype=torch.int32, device=dev)
+        csr = coop.make_csr(ro, col)
+        f = lambda: coop.coop_bfs(ctx, csr, 0, lv, stream=stream)
+        for _ in range(3):
+            f()
+        ms, kus = timed(f, max(3, args.steps))
+        ok = bool(np.array_equal(lv.cpu().numpy(), np.add(*np.divmod(np.arange(65536), 256))))
+        return {"levels": 511, "ms": round(ms, 4), "kernel_us": round(kus, 2), "us_per_level": round(kus / 511, 3),
+                "closed_form_ok": ok}
+
+    def barriers():
+        # empty resizing barriers: at M = N, at M = N/2 (half the CTAs lent), and at M = N
+        # with a forced schedule that kills or forks at about one barrier in eight
+        n = 20000
+        N = coop.coop_query(ctx)["max_ctas"]
+        f = lambda: coop.coop_barrier_bench(ctx, n, stream=stream, stats=False)
+
+        def per_barrier():
+            f()
+            _, kus = timed(f, 3)
+            return round(kus / n, 4)
+
+        res = {"barrier_us": per_barrier()}
+        got = coop.coop_request_resources(ctx, N // 2)
+        res["barrier_us_half"] = per_barrier()
+        coop.coop_release(ctx, got)
+        coop.coop_set_schedule(ctx, 7, p_kill=1.0 / 16, p_fork=1.0 / 16)
+        us = per_barrier()
+        st = coop.coop_get_stats(ctx)
+        coop.coop_set_schedule(ctx, 0, 0.0, 0.0)
+        res["barrier_us_resizing"] = {"us": us, "kills": st.kills, "forks": st.forks, "barriers": st.barriers,
+                                      "min_active": st.min_active}
+        return res
+
+    guarded(None, rmat22, "bfs_rmat22")
+    guarded("grid_bfs", grid)
+    guarded("preemption", lambda: preemption(coop, ctx, dev, stream))
+    guarded("gather_by_kill_mode", lambda: gather_by_kill_mode(coop, ctx, dev, stream))
+    guarded("topology_driven_sssp", lambda: topology_driven(coop, ctx, dev, stream, flush))
+    guarded("octree", lambda: octree(coop, ctx, dev, stream, flush))
+    guarded("batched", lambda: batched(coop, ctx, dev, stream, flush))
+    guarded("serving", lambda: serving(coop, dev))
+    guarded(None, barriers, "barrier_us")
     return out
 
 
