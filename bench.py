@@ -51,8 +51,8 @@ WORKLOADS = {
 # workload, from the ncu captures summarised in profiles/; an entry is used only while
 # the kernel sources still have the digest it was taken on (otherwise null).
 TRAFFIC = {
-    "rmat20-sssp": {"sources_sha": "4d552d6391af2f3c", "bytes": 373007872},
-    "rmat22-bfs": {"sources_sha": "4d552d6391af2f3c", "bytes": 392425728},
+    "rmat20-sssp": {"sources_sha": "e1957cbb1bd1f7a4", "bytes": 377867264},
+    "rmat22-bfs": {"sources_sha": "e1957cbb1bd1f7a4", "bytes": 391131904},
 }
 
 

@@ -328,8 +328,9 @@ coop_status coop_server_wait(coop_server *sv, uint64_t ticket, int timeout_us, c
 
 /*
  * Take n_ctas CTAs for a co-running task: CTAs no running query holds count first, the
- * rest is requested from the running queries, largest share first (each keeps at least
- * one).  Blocks like coop_request_resources, at most timeout_us per query; returns
+ * rest is requested from the running queries in proportion to what each can lend (each
+ * keeps at least one), all requests posted before any is waited for.  Blocks like
+ * coop_request_resources, at most timeout_us in all (timeout_us <= 0: no limit); returns
  * COOP_ETIMEOUT with *n_freed < n_ctas if fewer could be freed in time (the requests stay
  * pending).  The n_ctas are held for the co-runner either way until coop_server_release.
  */

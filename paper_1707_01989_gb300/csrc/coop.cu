@@ -1497,6 +1497,48 @@ void finalize_locked(coop_ctx *c) {
   store_release(&c->mbox->freed, c->served);
 }
 
+// The two halves of coop_request_resources.  post_kill raises the cumulative request by
+// n (offer_kill asked of the running kernel) and returns the count the device's `freed`
+// must reach; with no traversal in flight the request is granted at once (*granted).
+coop_status post_kill(coop_ctx *c, int n, uint32_t *target, bool *granted) {
+  std::lock_guard<std::mutex> lk(c->mu);
+  finalize_locked(c);
+  const int outstanding = (int)(c->kill_req - c->returned);
+  if (outstanding + n > c->N - 1) return COOP_EINVAL;
+  c->kill_req += (uint32_t)n;
+  *target = c->kill_req;
+  store_release(&c->mbox->kill_req, c->kill_req);
+  *granted = !running(c);
+  if (*granted) finalize_locked(c);
+  return COOP_OK;
+}
+
+// Waits until the device has freed the CTAs of a posted request (or the traversal ended,
+// which grants the rest), or until `deadline`; *got = the request's CTAs freed so far.
+coop_status wait_kill(coop_ctx *c, uint32_t target, int n, bool bounded,
+                      std::chrono::steady_clock::time_point deadline, int *got) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (uint32_t spin = 0;; ++spin) {
+    const uint32_t f = load_acquire(&c->mbox->freed);
+    *got = std::max(0, std::min(n, (int)(f - (target - (uint32_t)n))));
+    if ((int32_t)(f - target) >= 0) break;
+    if ((spin & 63u) == 0u) {
+      std::lock_guard<std::mutex> lk(c->mu);
+      if (!running(c)) {
+        finalize_locked(c);
+        break;
+      }
+    }
+    if (bounded && std::chrono::steady_clock::now() > deadline) return COOP_ETIMEOUT;
+    if (spin > 2048) std::this_thread::yield();
+  }
+  *got = n;
+  const double us = std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count();
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->gather_us_max = std::max(c->gather_us_max, us);
+  return COOP_OK;
+}
+
 coop_status ensure_scratch(coop_ctx *c, int64_t V, int64_t E) {
   const int64_t chunks = E / kIndexEdges + 2;
   if (V <= c->cap_V && chunks <= c->cap_chunks) return COOP_OK;
@@ -1821,48 +1863,19 @@ coop_status coop_barrier_bench(coop_ctx *c, int32_t n_barriers, int32_t never_ar
 coop_status coop_request_resources(coop_ctx *c, int n, int timeout_us, int *n_freed) {
   if (n_freed) *n_freed = 0;
   if (!c || n < 1) return COOP_EINVAL;
-  uint32_t target;
-  {
-    std::lock_guard<std::mutex> lk(c->mu);
-    finalize_locked(c);
-    const int outstanding = (int)(c->kill_req - c->returned);
-    if (outstanding + n > c->N - 1) return COOP_EINVAL;
-    c->kill_req += (uint32_t)n;
-    target = c->kill_req;
-    store_release(&c->mbox->kill_req, c->kill_req);
-    if (!running(c)) {
-      finalize_locked(c);
-      if (n_freed) *n_freed = n;
-      return COOP_OK;
-    }
+  uint32_t target = 0;
+  bool granted = false;
+  const coop_status st = post_kill(c, n, &target, &granted);
+  if (st != COOP_OK) return st;
+  if (granted) {
+    if (n_freed) *n_freed = n;
+    return COOP_OK;
   }
-  const auto t0 = std::chrono::steady_clock::now();
-  for (uint32_t spin = 0;; ++spin) {
-    const uint32_t f = load_acquire(&c->mbox->freed);
-    const int got = std::max(0, std::min(n, (int)(f - (target - (uint32_t)n))));
-    if ((int32_t)(f - target) >= 0) {
-      if (n_freed) *n_freed = n;
-      break;
-    }
-    if ((spin & 63u) == 0u) {
-      std::lock_guard<std::mutex> lk(c->mu);
-      if (!running(c)) {
-        finalize_locked(c);
-        if (n_freed) *n_freed = n;
-        break;
-      }
-    }
-    const double us = std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count();
-    if (timeout_us > 0 && us > (double)timeout_us) {
-      if (n_freed) *n_freed = got;
-      return COOP_ETIMEOUT;
-    }
-    if (spin > 2048) std::this_thread::yield();
-  }
-  const double us = std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count();
-  std::lock_guard<std::mutex> lk(c->mu);
-  c->gather_us_max = std::max(c->gather_us_max, us);
-  return COOP_OK;
+  int got = 0;
+  const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(std::max(0, timeout_us));
+  const coop_status w = wait_kill(c, target, n, timeout_us > 0, deadline, &got);
+  if (n_freed) *n_freed = got;
+  return w;
 }
 
 coop_status coop_release(coop_ctx *c, int n) {
@@ -2601,8 +2614,15 @@ coop_status coop_server_wait(coop_server *sv, uint64_t ticket, int timeout_us, c
 coop_status coop_server_request_resources(coop_server *sv, int n_ctas, int timeout_us, int *n_freed) {
   if (n_freed) *n_freed = 0;
   if (!sv || n_ctas < 1) return COOP_EINVAL;
-  std::vector<std::pair<coop_ctx *, int>> asks;
+  struct Ask {
+    coop_ctx *ctx;
+    int n;
+    uint32_t target;
+    bool granted;
+  };
+  std::vector<Ask> asks;
   int from_idle = 0;
+  coop_status worst = COOP_OK;
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     if (sv->corunner_held + n_ctas > sv->N - sv->min_share) return COOP_EINVAL;
@@ -2615,25 +2635,52 @@ coop_status coop_server_request_resources(coop_server *sv, int n_ctas, int timeo
         held += sv->slots[i].share;
       }
     from_idle = std::min(n_ctas, std::max(0, sv->N - held));
-    int need = n_ctas - from_idle;
-    // the rest from the running queries, largest share first
+    // The rest from the running queries in proportion to what each can lend, so that every
+    // query keeps the same fraction of its share.  CTAs taken from a query leave at its
+    // next offer_kill point, but CTAs given back join it only at its next barrier: a query
+    // cut down to its master CTA in the middle of a wide level would finish that level
+    // alone, long after the co-runner has returned the CTAs.
     std::sort(idx.begin(), idx.end(), [&](size_t x, size_t y) { return sv->slots[x].share > sv->slots[y].share; });
-    for (size_t i : idx) {
-      if (need <= 0) break;
-      auto &sl = sv->slots[i];
-      const int take = std::min(std::min(need, sl.share - sv->min_share), lendable(sl.ctx));
-      if (take <= 0) continue;
-      sl.share -= take;
-      need -= take;
-      asks.push_back({sl.ctx, take});
+    std::vector<int> room(idx.size()), take(idx.size(), 0);
+    int total = 0;
+    for (size_t j = 0; j < idx.size(); ++j) {
+      const auto &sl = sv->slots[idx[j]];
+      room[j] = std::max(0, std::min(sl.share - sv->min_share, lendable(sl.ctx)));
+      total += room[j];
+    }
+    const int need = std::min(n_ctas - from_idle, total);
+    int left = need;
+    for (size_t j = 0; j < idx.size() && total > 0; ++j) {
+      take[j] = (int)((int64_t)need * room[j] / total);
+      left -= take[j];
+    }
+    // the remainder one CTA at a time, largest shares first (need <= total: it ends)
+    for (size_t j = 0; left > 0; j = (j + 1) % idx.size())
+      if (take[j] < room[j]) {
+        ++take[j];
+        --left;
+      }
+    // every request is posted before any is waited for: the queries free their CTAs
+    // concurrently, within one deadline
+    for (size_t j = 0; j < idx.size(); ++j) {
+      if (take[j] <= 0) continue;
+      auto &sl = sv->slots[idx[j]];
+      Ask a{sl.ctx, take[j], 0u, false};
+      const coop_status st = post_kill(sl.ctx, a.n, &a.target, &a.granted);
+      if (st != COOP_OK) {
+        if (worst == COOP_OK) worst = st;
+        continue;
+      }
+      sl.share -= take[j];
+      asks.push_back(a);
     }
     sv->corunner_held += n_ctas;
   }
   int got = from_idle;
-  coop_status worst = COOP_OK;
+  const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(std::max(0, timeout_us));
   for (auto &a : asks) {
-    int f = 0;
-    const coop_status st = coop_request_resources(a.first, a.second, timeout_us, &f);
+    int f = a.n;
+    const coop_status st = a.granted ? COOP_OK : wait_kill(a.ctx, a.target, a.n, timeout_us > 0, deadline, &f);
     got += f;
     if (st != COOP_OK && worst == COOP_OK) worst = st;
   }
