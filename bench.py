@@ -51,8 +51,8 @@ WORKLOADS = {
 # workload, from the ncu captures summarised in profiles/; an entry is used only while
 # the kernel sources still have the digest it was taken on (otherwise null).
 TRAFFIC = {
-    "rmat20-sssp": {"sources_sha": "e1957cbb1bd1f7a4", "bytes": 377867264},
-    "rmat22-bfs": {"sources_sha": "e1957cbb1bd1f7a4", "bytes": 391131904},
+    "rmat20-sssp": {"sources_sha": "14fea7ef3ede4bdc", "bytes": 376828672},
+    "rmat22-bfs": {"sources_sha": "14fea7ef3ede4bdc", "bytes": 391368960},
 }
 
 
@@ -242,9 +242,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat20-sssp", choices=sorted(WORKLOADS))
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary workloads")
+    ap.add_argument("--extras", default="all",
+                    help="comma-separated secondary figures to run (default all): " + ", ".join(EXTRAS))
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--threads", type=int, default=0, help="worker threads per CTA (0 = library default)")
     args = ap.parse_args()
+    selected_extras(args.extras)  # an unknown name fails before any work
     if args.impl == "reference":
         return run_reference(args)
 
@@ -927,6 +930,21 @@ def serving(coop, dev, n_graphs=32, rate=200.0, duration_s=3.0, slots=4, budget=
             "all_ok": all(r.status == 0 for r in done)}
 
 
+EXTRAS = ("bfs_rmat22", "grid_bfs", "preemption", "gather_by_kill_mode", "topology_driven_sssp", "octree",
+          "batched", "serving", "barrier_us")
+
+
+def selected_extras(spec: str):
+    """The secondary figures named by --extras, in their fixed order ("all" = every one)."""
+    if spec.strip() == "all":
+        return EXTRAS
+    names = [x.strip() for x in spec.split(",") if x.strip()]
+    bad = [x for x in names if x not in EXTRAS]
+    if bad:
+        raise SystemExit(f"unknown --extras {bad}; choose from {', '.join(EXTRAS)}")
+    return tuple(x for x in EXTRAS if x in names)
+
+
 def secondary(coop, ctx, dev, stream, flush, args):
     """BFS on R-MAT 22, grid BFS, the co-runner with and without cooperation, batching,
     serving, barrier latency and the non-cooperative baseline ratio.  Each part runs on
@@ -1037,15 +1055,21 @@ def secondary(coop, ctx, dev, stream, flush, args):
                                       "min_active": st.min_active}
         return res
 
-    guarded(None, rmat22, "bfs_rmat22")
-    guarded("grid_bfs", grid)
-    guarded("preemption", lambda: preemption(coop, ctx, dev, stream))
-    guarded("gather_by_kill_mode", lambda: gather_by_kill_mode(coop, ctx, dev, stream))
-    guarded("topology_driven_sssp", lambda: topology_driven(coop, ctx, dev, stream, flush))
-    guarded("octree", lambda: octree(coop, ctx, dev, stream, flush))
-    guarded("batched", lambda: batched(coop, ctx, dev, stream, flush))
-    guarded("serving", lambda: serving(coop, dev))
-    guarded(None, barriers, "barrier_us")
+    parts = {
+        "bfs_rmat22": lambda: guarded(None, rmat22, "bfs_rmat22"),
+        "grid_bfs": lambda: guarded("grid_bfs", grid),
+        "preemption": lambda: guarded("preemption", lambda: preemption(coop, ctx, dev, stream)),
+        "gather_by_kill_mode": lambda: guarded("gather_by_kill_mode", lambda: gather_by_kill_mode(coop, ctx, dev, stream)),
+        "topology_driven_sssp": lambda: guarded("topology_driven_sssp",
+                                                lambda: topology_driven(coop, ctx, dev, stream, flush)),
+        "octree": lambda: guarded("octree", lambda: octree(coop, ctx, dev, stream, flush)),
+        "batched": lambda: guarded("batched", lambda: batched(coop, ctx, dev, stream, flush)),
+        "serving": lambda: guarded("serving", lambda: serving(coop, dev)),
+        "barrier_us": lambda: guarded(None, barriers, "barrier_us"),
+    }
+    assert tuple(parts) == EXTRAS
+    for name in selected_extras(args.extras):
+        parts[name]()
     return out
 
 

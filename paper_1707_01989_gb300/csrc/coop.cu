@@ -605,14 +605,45 @@ __device__ __forceinline__ void scheduler_warp(const Params &p, const volatile i
   }
 }
 
+// p-sssp relax of edges [e0, e1) of one row whose source distance is du, by the 32 lanes
+// of a warp, two edges per lane in flight.
+__device__ __forceinline__ void relax_edges(const Params &p, uint32_t *cost, uint32_t du, uint32_t e0, uint32_t e1,
+                                            unsigned lane, bool &bad, bool &ovf) {
+  const uint32_t V = (uint32_t)p.V;
+  for (uint32_t e00 = e0; e00 < e1; e00 += 64u) {
+    uint32_t v[2], wt[2];
+    bool ok[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const uint32_t e = e00 + 32u * (uint32_t)k + lane;
+      ok[k] = e < e1;
+      v[k] = ok[k] ? (uint32_t)__ldg(p.col + e) : 0u;
+      wt[k] = ok[k] ? __ldg(p.w + e) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      if (!ok[k]) continue;
+      if (v[k] >= V) {
+        bad = true;
+        continue;
+      }
+      const uint64_t nd = (uint64_t)du + (uint64_t)wt[k];
+      if (nd >= 0xFFFFFFFFull) ovf = true;
+      else if ((uint32_t)nd < cost[v[k]]) atomicMin(cost + v[k], (uint32_t)nd);
+    }
+  }
+}
+
 // Topology-driven SSSP, one interval of an iteration (Table 1, p-sssp: three resizing
 // barriers per iteration).  cost[] lives in the packed-word scratch, the "changed" flags
 // in the bitmap.  Work is partitioned by logical id as in Fig. 4, recomputed from the
 // current M: warp id * NW + w of stride M * NW, 32 vertices at a time.
 //   relax  (level % 3 == 0): every vertex lowered by the last update relaxes its
-//          out-edges into cost[] (atomicMin);
+//          out-edges into cost[] (atomicMin); rows of at least kTopoHeavy edges come
+//          from the update's chunk list, dealt out over every warp of the grid;
 //   update (level % 3 == 1): dist = min(dist, cost); the flags of the next relax are the
-//          vertices lowered now; the number lowered is counted;
+//          vertices lowered now, and the heavy rows among them are listed as chunks; the
+//          number lowered is counted;
 //   check  (level % 3 == 2): no work -- the releaser ends the run when the update
 //          lowered nothing.
 template <int NW>
@@ -622,11 +653,29 @@ __device__ __forceinline__ void topo_interval(const Params &p, const Interval &i
   uint32_t *cost = reinterpret_cast<uint32_t *>(p.ds);
   const uint32_t phase = (uint32_t)iv.level % 3u;
   if (phase == 0u) {
-    // warp-cooperative rows: warp id * NW + w takes 32 vertices at a time; for each flagged
-    // one, the 32 lanes stride over its out-edges (a thread per vertex would leave an
-    // R-MAT hub's 10^5 edges to one thread)
     unsigned long long nrel = 0ull;
     bool bad = false, ovf = false;
+    // heavy rows first: chunk j of the list (built by the update interval that flagged
+    // the rows) goes to warp j mod G of the grid
+    const uint32_t G = (uint32_t)iv.M * NW;
+    const uint32_t nch = p.topo_heavy ? min(ld_relaxed(&p.ctl->cursor.v), V) : 0u;
+    for (uint32_t j = (uint32_t)id * NW + (threadIdx.x >> 5); j < nch; j += G) {
+      const uint32_t u = p.qv[0][j], e0 = p.qs[0][j];
+      if (u >= V) {
+        bad = true;
+        continue;
+      }
+      const int32_t b = __ldg(p.row_off + u + 1);
+      if (b < 0 || (uint32_t)b > p.E || e0 >= (uint32_t)b) {
+        bad = true;
+        continue;
+      }
+      const uint32_t e1 = min((uint32_t)b, e0 + kTopoChunk);  // b < 2^31: no wrap
+      nrel += (unsigned long long)(e1 - e0);
+      relax_edges(p, cost, p.dist[u], e0, e1, lane, bad, ovf);
+    }
+    // the other flagged rows, warp-cooperatively: warp id * NW + w takes 32 vertices at a
+    // time; for each flagged one, the 32 lanes stride over its out-edges
     for (uint32_t base = ((uint32_t)id * NW + (threadIdx.x >> 5)) * 32u; base < V;
          base += (uint32_t)iv.M * NW * 32u) {
       unsigned m = p.visited[base >> 5];
@@ -634,36 +683,14 @@ __device__ __forceinline__ void topo_interval(const Params &p, const Interval &i
       while (m) {
         const uint32_t u = base + (uint32_t)(__ffs(m) - 1);
         m &= m - 1u;
-        const uint32_t du = p.dist[u];
         const int32_t a = __ldg(p.row_off + u), b = __ldg(p.row_off + u + 1);
         if (a < 0 || b < a || (uint32_t)b > p.E) {
           bad = true;
           continue;
         }
+        if (p.topo_heavy && (uint32_t)(b - a) >= kTopoHeavy) continue;  // listed: relaxed above
         nrel += (unsigned long long)(b - a);
-        for (int32_t e0 = a; e0 < b; e0 += 64) {
-          // two edges per lane in flight
-          uint32_t v[2], wt[2];
-          bool ok[2];
-#pragma unroll
-          for (int k = 0; k < 2; ++k) {
-            const int32_t e = e0 + 32 * k + (int32_t)lane;
-            ok[k] = e < b;
-            v[k] = ok[k] ? (uint32_t)__ldg(p.col + e) : 0u;
-            wt[k] = ok[k] ? __ldg(p.w + e) : 0u;
-          }
-#pragma unroll
-          for (int k = 0; k < 2; ++k) {
-            if (!ok[k]) continue;
-            if (v[k] >= V) {
-              bad = true;
-              continue;
-            }
-            const uint64_t nd = (uint64_t)du + (uint64_t)wt[k];
-            if (nd >= 0xFFFFFFFFull) ovf = true;
-            else if ((uint32_t)nd < cost[v[k]]) atomicMin(cost + v[k], (uint32_t)nd);
-          }
-        }
+        relax_edges(p, cost, p.dist[u], (uint32_t)a, (uint32_t)b, lane, bad, ovf);
       }
     }
     if (lane == 0 && nrel) atomicAdd(&p.ctl->qctr[1], nrel);
@@ -681,9 +708,23 @@ __device__ __forceinline__ void topo_interval(const Params &p, const Interval &i
         if (cv < dv) {
           p.dist[v] = cv;
           low = true;
+          const int32_t a = __ldg(p.row_off + v), b = __ldg(p.row_off + v + 1);
           if (dv == 0xFFFFFFFFu) {  // first time reached
             nreach += 1u;
-            ereach += (unsigned long long)(__ldg(p.row_off + v + 1) - __ldg(p.row_off + v));
+            ereach += (unsigned long long)(b - a);
+          }
+          // a heavy row flagged for the next relax is listed there as chunks
+          if (p.topo_heavy && a >= 0 && b >= a && (uint32_t)b <= p.E && (uint32_t)(b - a) >= kTopoHeavy) {
+            const uint32_t n = ((uint32_t)(b - a) + kTopoChunk - 1u) / kTopoChunk;
+            const uint32_t at = atomicAdd(&p.ctl->cursor.v, n);
+            if (at > V || n > V - at) {
+              raise_err(p, ERR_GRAPH);  // only rows that overlap can outgrow the list
+            } else {
+              for (uint32_t k = 0; k < n; ++k) {
+                p.qv[0][at + k] = v;
+                p.qs[0][at + k] = (uint32_t)a + k * kTopoChunk;
+              }
+            }
           }
         }
       }
@@ -1630,6 +1671,9 @@ coop_status launch_run(coop_ctx *c, const coop_csr *g, const uint32_t *w, int32_
       p.col = g->col;
       p.V = g->num_vertices;
       p.E = (uint32_t)g->num_edges;
+      // p-sssp's heavy-row chunk list lives in queue 0 (at least V entries)
+      const uint64_t E = (uint64_t)g->num_edges;
+      p.topo_heavy = (MODE == MODE_PSSSP && E / kTopoChunk + E / kTopoHeavy + 1 <= (uint64_t)g->num_vertices) ? 1u : 0u;
     }
     p.w = w;
     p.level = level;

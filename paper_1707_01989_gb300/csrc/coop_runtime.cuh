@@ -60,6 +60,12 @@ constexpr uint32_t kChunkUnitsMax = 16;     // a work chunk spans 1..16 32-edge 
 // bulk are far slower than loads).  On smaller frontiers the read is one more dependent
 // round trip on the level's critical path, and the claim goes straight to the atomic.
 constexpr uint32_t kPrecheckEdges = 65536;
+// p-sssp: a flagged row of at least kTopoHeavy edges is not relaxed by the one warp whose
+// vertex stripe holds it but listed, as chunks of kTopoChunk edges, by the update interval
+// that flagged it; the relax interval deals the chunks out over every warp of the grid.
+// (An R-MAT hub's 10^4-10^5 edges on one warp would leave the rest of the grid waiting.)
+constexpr uint32_t kTopoHeavy = 2048;
+constexpr uint32_t kTopoChunk = 256;
 
 // MODE_PSSSP: topology-driven SSSP (Table 1's p-sssp, read as Pannotia's formulation):
 // every iteration scans all vertices in three intervals -- relax, update, check.
@@ -204,6 +210,10 @@ struct Params {
   uint32_t coop;       // 0: non-cooperative baseline (fixed ids, no scheduler)
   uint32_t kill_mode;  // where host requests are served: KILL_CHUNK, KILL_QUERY or KILL_SIMPLE
   int32_t mode;        // MODE_BFS / MODE_SSSP (read by the batch kernel)
+  // MODE_PSSSP: heavy rows are listed as chunks in queue 0 (qv: vertex, qs: first edge),
+  // their count in ctl->cursor.  Set only when the list cannot outgrow the queue:
+  // E / kTopoChunk + E / kTopoHeavy + 1 <= V.
+  uint32_t topo_heavy;
 };
 
 struct CtaShared {
@@ -467,6 +477,8 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
       c->qctr[0] = 0ull;
       c->qctr[1] = 0ull;
     }
+    // the relax interval has used the heavy-row list: the next update builds it anew
+    if ((uint32_t)cur.level % 3u == 0u) c->cursor.v = 0u;
   } else {
     count = (uint32_t)(packed >> 32);
     edges = (uint32_t)packed;
@@ -681,6 +693,14 @@ __device__ __forceinline__ void master_enter(const Params &p, CtaShared &cs) {
       c->reached_edges = (unsigned long long)(re - rs);
       if (MODE == MODE_PSSSP) {
         count = 1u;  // the iterations run until one lowers nothing
+        if (p.topo_heavy && (uint32_t)(re - rs) >= kTopoHeavy) {
+          uint32_t n = 0u;
+          for (uint64_t e = (uint64_t)rs; e < (uint64_t)re; e += kTopoChunk, ++n) {
+            p.qv[0][n] = (uint32_t)s;
+            p.qs[0][n] = (uint32_t)e;
+          }
+          c->cursor.v = n;
+        }
       } else if (re > rs) {
         p.qo[0][0] = 0u;
         p.qs[0][0] = (uint32_t)rs;

@@ -41,3 +41,31 @@ def assert_same(got, exp, what):
     assert got.shape == exp.shape, (what, got.shape, exp.shape)
     bad = np.flatnonzero(got != exp)
     assert bad.size == 0, f"{what}: {bad.size} mismatches, first at {bad[0]}: got {got[bad[0]]} expected {exp[bad[0]]}"
+
+
+def hub_graph(seed, n=20000, hubs=(2048, 2300, 5000, 9000), base_edges=60000):
+    """A sparse random graph on n vertices with heavy rows: hub i (vertex 1 + i) has
+    hubs[i] out-edges.  Vertex 0 reaches every hub twice -- by a direct edge of weight 255
+    and later by a two-edge path of weight 2 -- so shortest-path relaxation lowers each
+    hub in two different iterations.  Returns (graph, weights in CSR order, source 0)."""
+    import graphgen as gg
+    rng = np.random.default_rng(seed)
+    src = [rng.integers(0, n, base_edges)]
+    dst = [rng.integers(0, n, base_edges)]
+    want = {}
+    for i, d in enumerate(hubs):
+        h, mid = 1 + i, 1 + len(hubs) + i
+        src.append(np.full(d, h))
+        dst.append(rng.choice(n, size=d, replace=False))
+        src.append(np.array([0, 0, mid]))
+        dst.append(np.array([h, mid, h]))
+        want[(0, h)], want[(0, mid)], want[(mid, h)] = 255, 1, 1
+    g = gg.from_edges(n, np.concatenate(src), np.concatenate(dst), name=f"hubs{seed}")
+    w = gg.weights(g, seed + 1)
+    ro, col = np.array(g.row_off), np.array(g.col)
+    for (u, v), x in want.items():
+        row = col[ro[u]:ro[u + 1]]
+        k = int(np.searchsorted(row, v))
+        assert k < row.size and row[k] == v
+        w[ro[u] + k] = x
+    return g, w, 0

@@ -15,7 +15,7 @@ import pytest
 import graphgen as gg
 import oracle
 import paper_1707_01989_gb300 as coop
-from gpu_util import DevGraph, assert_same, run_bfs, run_sssp
+from gpu_util import DevGraph, assert_same, hub_graph, run_bfs, run_sssp
 from oracle.semantics import replay_resize_log
 
 pytestmark = pytest.mark.gpu
@@ -302,6 +302,23 @@ def test_topology_driven_sssp_under_schedules(ctx, seed):
     st = coop.coop_sssp_topo(ctx, dg.csr, dg.w, src, out, stats=True)
     coop.coop_set_schedule(ctx, 0, 0.0, 0.0)
     assert_same(out.cpu().numpy().view(np.uint32), oracle.dijkstra(g, w, src), f"p-sssp schedule {seed}")
+    assert st.kills > 0 or st.forks > 0
+    _replay(ctx, st)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_topology_driven_sssp_heavy_rows_under_schedules(ctx, seed):
+    """p-sssp whose heavy rows go through the chunk list, under forced kill/fork
+    schedules: the chunks are dealt over whatever grid each relax interval has."""
+    g, w, src = hub_graph(10 + seed)
+    dg = DevGraph(g, w)
+    coop.coop_set_schedule(ctx, 600 + seed, p_kill=0.3, p_fork=0.4)
+    out = dg.empty()
+    try:
+        st = coop.coop_sssp_topo(ctx, dg.csr, dg.w, src, out, stats=True)
+    finally:
+        coop.coop_set_schedule(ctx, 0, 0.0, 0.0)
+    assert_same(out.cpu().numpy().view(np.uint32), oracle.dijkstra(g, w, src), f"p-sssp hubs schedule {seed}")
     assert st.kills > 0 or st.forks > 0
     _replay(ctx, st)
 

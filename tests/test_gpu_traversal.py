@@ -11,7 +11,7 @@ import pytest
 import graphgen as gg
 import oracle
 import paper_1707_01989_gb300 as coop
-from gpu_util import DevGraph, assert_same, run_bfs, run_sssp
+from gpu_util import DevGraph, assert_same, hub_graph, run_bfs, run_sssp
 
 pytestmark = pytest.mark.gpu
 
@@ -233,6 +233,31 @@ def test_topology_driven_sssp_matches_oracle(ctx, name):
     exp = oracle.dijkstra(g, w, src)
     assert_same(d, exp, f"p-sssp {name}")
     assert st.barriers % 3 == 0  # whole iterations: relax, update, check
+    assert st.vertices_reached == int((exp != 0xFFFFFFFF).sum())
+    assert st.reached_edges == oracle.traversal_work(g, exp != 0xFFFFFFFF)[1]
+
+
+@pytest.mark.parametrize("case", ["hubs", "star_center", "star_leaf", "dense_list_off"])
+def test_topology_driven_sssp_heavy_rows(ctx, case):
+    """p-sssp with rows of at least 2048 edges, which the update interval lists as
+    256-edge chunks for the next relax to deal out over the whole grid: hubs lowered in
+    two different iterations, the source itself heavy (listed at entry), a heavy row
+    reached through a leaf, and a dense graph where the list is off (it could outgrow
+    its V-entry queue) and the stripe scan relaxes every row."""
+    if case == "hubs":
+        g, w, src = hub_graph(3)
+    elif case.startswith("star"):
+        g = gg.star(6000)
+        w = gg.weights(g, 35)
+        src = 0 if case == "star_center" else 17
+    else:
+        g = gg.complete(2100)
+        w = gg.weights(g, 36)
+        src = 5
+    d, st = _run_topo(ctx, DevGraph(g, w), src)
+    exp = oracle.dijkstra(g, w, src)
+    assert_same(d, exp, f"p-sssp {case}")
+    assert st.barriers % 3 == 0
     assert st.vertices_reached == int((exp != 0xFFFFFFFF).sum())
     assert st.reached_edges == oracle.traversal_work(g, exp != 0xFFFFFFFF)[1]
 

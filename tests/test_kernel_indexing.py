@@ -189,3 +189,104 @@ def test_window_arithmetic_single_entry_and_exact_multiples():
     check_frontier(np.array([32]), 1, rng)
     check_frontier(np.array([32] * 10), 3, rng)
     check_frontier(np.array([31, 1, 33, 64, 1, 1]), 7, rng)
+
+
+# ---- p-sssp relax interval: heavy rows as a chunk list dealt out over the grid --------
+TOPO_HEAVY, TOPO_CHUNK = 2048, 256  # kTopoHeavy, kTopoChunk
+
+
+def topo_heavy_enabled(V, E):
+    """The host's condition for listing heavy rows (the list lives in a V-entry queue)."""
+    return E // TOPO_CHUNK + E // TOPO_HEAVY + 1 <= V
+
+
+def relax_edges_cover(cnt, e0, e1):
+    """relax_edges: 32 lanes, two edges per lane in flight, steps of 64 edges."""
+    if e1 <= e0:
+        return
+    e = (np.arange(e0, e1, 64)[:, None, None] + 32 * np.arange(2)[None, :, None]
+         + np.arange(32)[None, None, :]).ravel()
+    np.add.at(cnt, e[e < e1], 1)
+
+
+def emulate_topo_relax(row_off, flagged, M, NW, rng):
+    """The update interval lists the flagged heavy rows (in any order: lanes race on the
+    counter); the relax interval deals chunk j to warp j mod G and every warp scans its
+    32-vertex stripes, skipping listed rows.  Returns relaxations per edge and the list
+    length."""
+    V, E = len(row_off) - 1, int(row_off[-1])
+    on = topo_heavy_enabled(V, E)
+    lst = []
+    for v in rng.permutation(np.asarray(flagged, dtype=np.int64)):
+        a, b = int(row_off[v]), int(row_off[v + 1])
+        if on and b - a >= TOPO_HEAVY:
+            n = (b - a + TOPO_CHUNK - 1) // TOPO_CHUNK
+            assert len(lst) + n <= V, "the list would outgrow its queue"
+            lst.extend((int(v), a + k * TOPO_CHUNK) for k in range(n))
+    fl = np.zeros(V, dtype=bool)
+    fl[np.asarray(flagged, dtype=np.int64)] = True
+    cnt = np.zeros(E, dtype=np.int64)
+    G = M * NW
+    nch = min(len(lst), V)
+    for gw in range(G):
+        for j in range(gw, nch, G):
+            u, e0 = lst[j]
+            b = int(row_off[u + 1])
+            assert 0 <= u < V and e0 < b
+            relax_edges_cover(cnt, e0, min(b, e0 + TOPO_CHUNK))
+        for base in range(gw * 32, V, G * 32):
+            for u in np.flatnonzero(fl[base:base + 32]) + base:
+                a, b = int(row_off[u]), int(row_off[u + 1])
+                if on and b - a >= TOPO_HEAVY:
+                    continue
+                relax_edges_cover(cnt, a, b)
+    return cnt, len(lst)
+
+
+def rows_with_degrees(degs):
+    return np.concatenate([[0], np.cumsum(degs)]).astype(np.int64)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_topo_heavy_rows_relaxed_exactly_once(seed):
+    """Every edge of a flagged row is relaxed once (heavy rows through the chunk list,
+    the others by the stripe scan), no other edge is, for grids of any size."""
+    rng = np.random.default_rng(700 + seed)
+    V = int(rng.integers(3000, 9000))
+    degs = rng.integers(0, 12, size=V)
+    hubs = rng.choice(V, size=int(rng.integers(1, 6)), replace=False)
+    degs[hubs] = rng.integers(TOPO_HEAVY - 1, 4 * TOPO_HEAVY + 300, size=len(hubs))
+    degs[hubs[0]] = TOPO_HEAVY  # exactly at the threshold
+    row_off = rows_with_degrees(degs)
+    assert topo_heavy_enabled(V, int(row_off[-1]))
+    flagged = np.union1d(rng.choice(V, size=V // 5, replace=False), hubs[: max(1, len(hubs) - 1)])
+    M, NW = int(rng.integers(1, 5)), int(rng.choice([1, 3, 31]))
+    cnt, n_list = emulate_topo_relax(row_off, flagged, M, NW, rng)
+    want = np.zeros_like(cnt)
+    for v in flagged:
+        want[row_off[v]:row_off[v + 1]] = 1
+    assert np.array_equal(cnt, want)
+    assert n_list > 0
+
+
+def test_topo_heavy_list_bound_is_tight_but_safe():
+    """Adversarial degree sequences at the host's condition: every row heavy and flagged
+    (2048 edges: 8 chunks each; 2049 edges: 9 chunks each) still fits the V-entry queue."""
+    rng = np.random.default_rng(5)
+    for d in (TOPO_HEAVY, TOPO_HEAVY + 1, TOPO_HEAVY + TOPO_CHUNK - 1, 3 * TOPO_HEAVY + 1):
+        H = 7
+        E = H * d
+        V = E // TOPO_CHUNK + E // TOPO_HEAVY + 1  # the smallest V the host accepts
+        degs = np.zeros(V, dtype=np.int64)
+        degs[:H] = d
+        row_off = rows_with_degrees(degs)
+        cnt, n_list = emulate_topo_relax(row_off, np.arange(H), 1, 2, rng)
+        assert n_list <= V
+        assert np.all(cnt == 1)
+    # one vertex fewer and the host turns the list off: the stripe scan relaxes everything
+    degs = np.zeros(V - 1, dtype=np.int64)
+    degs[:H] = d
+    row_off = rows_with_degrees(degs)
+    assert not topo_heavy_enabled(V - 1, int(row_off[-1]))
+    cnt, n_list = emulate_topo_relax(row_off, np.arange(H), 1, 2, rng)
+    assert n_list == 0 and np.all(cnt == 1)
