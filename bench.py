@@ -51,8 +51,8 @@ WORKLOADS = {
 # workload, from the ncu captures summarised in profiles/; an entry is used only while
 # the kernel sources still have the digest it was taken on (otherwise null).
 TRAFFIC = {
-    "rmat20-sssp": {"sources_sha": "14fea7ef3ede4bdc", "bytes": 376828672},
-    "rmat22-bfs": {"sources_sha": "14fea7ef3ede4bdc", "bytes": 391368960},
+    "rmat20-sssp": {"sources_sha": "cf783cdda4306f4f", "bytes": 373181696},
+    "rmat22-bfs": {"sources_sha": "cf783cdda4306f4f", "bytes": 391909888},
 }
 
 

@@ -64,7 +64,7 @@ constexpr uint32_t kPrecheckEdges = 65536;
 // vertex stripe holds it but listed, as chunks of kTopoChunk edges, by the update interval
 // that flagged it; the relax interval deals the chunks out over every warp of the grid.
 // (An R-MAT hub's 10^4-10^5 edges on one warp would leave the rest of the grid waiting.)
-constexpr uint32_t kTopoHeavy = 2048;
+constexpr uint32_t kTopoHeavy = 512;
 constexpr uint32_t kTopoChunk = 256;
 
 // MODE_PSSSP: topology-driven SSSP (Table 1's p-sssp, read as Pannotia's formulation):

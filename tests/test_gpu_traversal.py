@@ -239,7 +239,7 @@ def test_topology_driven_sssp_matches_oracle(ctx, name):
 
 @pytest.mark.parametrize("case", ["hubs", "star_center", "star_leaf", "dense_list_off"])
 def test_topology_driven_sssp_heavy_rows(ctx, case):
-    """p-sssp with rows of at least 2048 edges, which the update interval lists as
+    """p-sssp with rows of at least 512 edges, which the update interval lists as
     256-edge chunks for the next relax to deal out over the whole grid: hubs lowered in
     two different iterations, the source itself heavy (listed at entry), a heavy row
     reached through a leaf, and a dense graph where the list is off (it could outgrow

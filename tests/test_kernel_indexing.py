@@ -192,7 +192,7 @@ def test_window_arithmetic_single_entry_and_exact_multiples():
 
 
 # ---- p-sssp relax interval: heavy rows as a chunk list dealt out over the grid --------
-TOPO_HEAVY, TOPO_CHUNK = 2048, 256  # kTopoHeavy, kTopoChunk
+TOPO_HEAVY, TOPO_CHUNK = 512, 256  # kTopoHeavy, kTopoChunk
 
 
 def topo_heavy_enabled(V, E):
@@ -271,7 +271,8 @@ def test_topo_heavy_rows_relaxed_exactly_once(seed):
 
 def test_topo_heavy_list_bound_is_tight_but_safe():
     """Adversarial degree sequences at the host's condition: every row heavy and flagged
-    (2048 edges: 8 chunks each; 2049 edges: 9 chunks each) still fits the V-entry queue."""
+    (at the threshold, one edge over it, one edge short of a further chunk, and three
+    times over) still fits the V-entry queue."""
     rng = np.random.default_rng(5)
     for d in (TOPO_HEAVY, TOPO_HEAVY + 1, TOPO_HEAVY + TOPO_CHUNK - 1, 3 * TOPO_HEAVY + 1):
         H = 7
