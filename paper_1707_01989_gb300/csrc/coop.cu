@@ -90,6 +90,34 @@ __device__ __forceinline__ void load_entry(const Params &p, const uint32_t *qo, 
 // warp scan of the degrees for their edge-space offsets, and coalesced stores.
 constexpr int kStage = 64;
 
+// BFS claim candidates: targets whose visited bit read as clear are compacted into a
+// per-warp ring and claimed one per lane, so that the claim (atomic, level write, row
+// bounds, enqueue) runs once per 32 candidates with every lane busy, instead of once per
+// 32-edge group with a few lanes busy.  A ring holds at most 63 entries: whenever 32 are
+// pending after a group they are claimed at once; the rest when the warp's part of the
+// interval is done.  (Claiming what is pending at the end of every iteration instead
+// measured 8 % slower on R-MAT 22.)
+constexpr uint32_t kCand = 64;
+constexpr uint32_t kNoChunk = 0xFFFFFFFFu;  // no further chunk for this warp
+
+// The chunk schedule of one interval.  A frontier of at most GW * 32 edges (GW = M * NW
+// worker warps) gets one 32-edge chunk per warp.  A larger one is cut into units of
+// kIndexEdges edges, handed out in rounds of GW chunks: round r's chunks span
+// s_r = clamp(ceil(rem_r / (2 GW)), 1, cap) units each, rem_r being the units no earlier
+// round covered, so that each round takes about half of what is left.  Most of a wide
+// level then goes in large chunks (few chunk starts, each a chain of dependent loads) and
+// its end in single units (a short tail).  The cap is larger for BFS than for SSSP, whose
+// relaxations read distances at the start of a chunk: long chunks there expand more edges
+// (kChunkUnitsMax, kChunkUnitsMaxSssp).  Round 0's chunk j is warp j's -- Fig. 4's
+// tid/stride split, recomputed from the current M -- and later chunk ids come from the
+// shared cursor.  On wide levels every chunk starts at a unit boundary, an indexed edge.
+struct ChunkSched {  // per warp, in shared memory: touched only between chunks
+  uint32_t U;      // units of the interval
+  uint32_t shift;  // log2 of the edges per unit: 5 on small frontiers, else log2(kIndexEdges)
+  uint32_t k0, base, s;  // the current round: first chunk id, first unit, units per chunk
+  uint32_t cap;          // units per chunk at most
+};
+
 // Chunk index: for every unit boundary j*kIndexEdges inside an entry's edge range
 // [o, o + d), record the entry's queue slot.
 __device__ __forceinline__ void index_chunks(uint32_t *qx, uint32_t o, uint32_t d, uint32_t slot) {
@@ -162,6 +190,40 @@ __device__ __forceinline__ void stage_push(const Params &p, uint32_t out, WarpSt
   }
 }
 
+// Claim the n (<= 32) candidates at ring positions head.. of a BFS warp, one per lane:
+// the row bounds are read before the atomicOr so the two round trips overlap; a lane
+// whose atomicOr set the bit writes the level and enqueues the vertex if it has
+// out-edges.  A candidate that another warp claimed meanwhile costs one failed atomic.
+__device__ __forceinline__ void claim_batch(const Params &p, uint32_t out, WarpStage &stage, uint32_t &staged,
+                                            const uint32_t *cand, uint32_t head, uint32_t n, uint32_t next_level,
+                                            bool &bad, uint32_t &nreach, uint64_t &ereach, unsigned lane) {
+  __syncwarp();  // the ring's entries written by other lanes
+  const bool has = lane < n;
+  const uint32_t v = has ? cand[(head + lane) & (kCand - 1u)] : 0u;
+  int32_t ra = 0, rb = 0;
+  if (has) {
+    ra = __ldg(p.row_off + v);
+    rb = __ldg(p.row_off + v + 1);
+  }
+  const uint32_t m = 1u << (v & 31u);
+  const bool claim = has && (atomicOr(p.visited + (v >> 5), m) & m) == 0u;
+  uint32_t rs = 0u, deg = 0u;
+  bool push = false;
+  if (claim) {
+    p.level[v] = (int32_t)next_level;
+    if (ra < 0 || rb < ra || (uint32_t)rb > p.E) bad = true;
+    else {
+      rs = (uint32_t)ra;
+      deg = (uint32_t)(rb - ra);
+      push = deg > 0u;
+    }
+    nreach += 1u;
+    ereach += deg;
+  }
+  stage_push<MODE_BFS>(p, out, stage, staged, push, v, rs, deg, lane);
+  __syncwarp();  // the ring's slots just read may be written again by the next group
+}
+
 // Read row_off[v], row_off[v+1] of a vertex about to be enqueued; false if malformed.
 __device__ __forceinline__ bool row_of(const Params &p, uint32_t v, uint32_t &rs, uint32_t &deg) {
   const int32_t a = __ldg(p.row_off + v), b = __ldg(p.row_off + v + 1);
@@ -180,14 +242,17 @@ constexpr int kUnroll = 4;  // 32-edge groups a warp handles per iteration
 // claim.  Every lane copies and later reads only its own words of a slot.
 constexpr int kStages = 2;  // landing slots: copies run kStages - 1 iterations ahead
 template <int MODE>
-struct Landing {  // BFS (and the barrier self-test): columns only
+struct Landing {  // BFS (and the barrier self-test): columns, the claim ring, the schedule
   uint32_t col[kStages][kUnroll][32];
+  uint32_t cand[kCand];
+  ChunkSched sched;
 };
 template <>
 struct Landing<MODE_SSSP> {
   uint32_t col[kStages][kUnroll][32];
   uint32_t w[kStages][kUnroll][32];
   uint32_t du[kStages][kUnroll][32];
+  ChunkSched sched;
 };
 
 // Dynamic shared memory of a traversal CTA: NW enqueue stages, then NW landing buffers,
@@ -295,12 +360,84 @@ __device__ __forceinline__ void issue_groups(const Params &p, const uint32_t *qo
   cp_async_commit();
 }
 
-// Expand edges [c0, c1) of the interval's edge space; entry wb of the input queue holds
-// edge c0.  Software-pipelined over iterations of kUnroll 32-edge groups: the copies of
-// iteration i+1 are started, then iteration i's targets are claimed, so every lane keeps
+// BFS expansion of edges [c0, c1) (the contract is expand_range's).  Software-pipelined
+// like it; per iteration the visited word of every target is read (on small frontiers no
+// pre-check: every target is a candidate) and the targets it shows unvisited are
+// compacted into the warp's claim ring, 32 pending candidates claimed at once.  (Loading
+// the visited words one iteration ahead, with a third landing slot, measured no faster.)
+template <int MODE>
+__device__ __forceinline__ uint32_t expand_range_bfs(const Params &p, const Interval &iv, uint32_t c0, uint32_t c1,
+                                                     uint32_t wb, WarpStage &stage, Landing<MODE> &pf,
+                                                     uint32_t &staged, bool &bad, uint32_t &nreach, uint64_t &ereach,
+                                                     bool more, int32_t id, uint32_t GW, uint32_t &ch,
+                                                     uint32_t &ct) {
+  const unsigned lane = threadIdx.x & 31u;
+  const uint32_t Etot = iv.edges;
+  const uint32_t F = iv.count;
+  const uint32_t in = iv.sel, out = in ^ 1u;
+  const uint32_t *qo = in ? p.qo[1] : p.qo[0];
+  const uint32_t *qs = in ? p.qs[1] : p.qs[0];
+  const uint32_t *qv = in ? p.qv[1] : p.qv[0];
+  const unsigned lm_le = lanemask_le();
+  const unsigned lt = lm_le & ~(1u << lane);
+  const uint32_t next_level = (uint32_t)iv.level + 1u;
+  const uint32_t V = (uint32_t)p.V;
+  const uint32_t E1 = c1;
+  const bool pre = iv.precheck != 0u;
+  constexpr uint32_t kIt = 32u * kUnroll;
+
+  Window w;
+  load_entry<MODE>(p, qo, qs, qv, F, Etot, wb + lane, w);
+  while (slide<MODE>(p, qo, qs, qv, F, Etot, c0, w, wb, lane)) {
+  }
+  uint32_t ci = c0;
+#pragma unroll
+  for (int k = 0; k < kStages - 1; ++k, ci += kIt) {
+    if (ci < E1) issue_groups<MODE>(p, qo, qs, qv, F, Etot, ci, E1, w, wb, pf, k, lane, lm_le);
+    else cp_async_commit();
+  }
+  int sb = 0, sn = kStages - 1;
+  uint32_t jn = kNoChunk;
+  for (uint32_t c = c0; c < E1; c += kIt, ci += kIt) {
+    if (more && lane == 0 && c + kIt >= E1 &&
+        !(p.coop && p.kill_mode == KILL_CHUNK && doomed(ld_relaxed64(&p.ctl->kill_target), iv.epoch, id)))
+      jn = GW + atomicAdd(&p.ctl->cursor.v, 1u);
+    if (ci < E1) issue_groups<MODE>(p, qo, qs, qv, F, Etot, ci, E1, w, wb, pf, sn, lane, lm_le);
+    else cp_async_commit();
+    cp_async_wait<kStages - 1>();  // this iteration's slot has landed; later ones stay in flight
+    uint32_t vv[kUnroll], word[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      vv[u] = pf.col[sb][u][lane];
+      word[u] = 0xFFFFFFFFu;  // past the range or out of [0, V): reads as visited
+      if (c + 32u * (uint32_t)u + lane < E1) {
+        if (vv[u] >= V) bad = true;
+        else word[u] = pre ? *(p.visited + (vv[u] >> 5)) : 0u;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const bool cnd = word[u] != 0xFFFFFFFFu && ((word[u] >> (vv[u] & 31u)) & 1u) == 0u;
+      const unsigned m = __ballot_sync(kFull, cnd);
+      if (cnd) pf.cand[(ct + (uint32_t)__popc(m & lt)) & (kCand - 1u)] = vv[u];
+      ct += (uint32_t)__popc(m);
+      if (ct - ch >= 32u) {
+        claim_batch(p, out, stage, staged, pf.cand, ch, 32u, next_level, bad, nreach, ereach, lane);
+        ch += 32u;
+      }
+    }
+    sb = sb + 1 == kStages ? 0 : sb + 1;
+    sn = sn + 1 == kStages ? 0 : sn + 1;
+  }
+  return __shfl_sync(kFull, jn, 0);
+}
+
+// Expand edges [c0, c1) of the interval's edge space (SSSP); entry wb of the input queue
+// holds edge c0.  Software-pipelined over iterations of kUnroll 32-edge groups: the copies
+// of iteration i+1 are started, then iteration i's targets are relaxed, so every lane keeps
 // the next kUnroll column loads in flight while it works on the current ones.
 //
-// Returns the warp's next chunk (nchunks: none).  With `more`, lane 0 claims it from the
+// Returns the warp's next chunk id (kNoChunk: none).  With `more`, lane 0 claims it from the
 // cursor at the start of the range's last iteration, so the atomic's latency overlaps
 // that iteration's work.  This is also the offer_kill point of the expansion: a CTA inside
 // the host's kill target claims nothing more (the other CTAs take the rest of the level)
@@ -309,8 +446,7 @@ template <int MODE>
 __device__ __forceinline__ uint32_t expand_range(const Params &p, const Interval &iv, uint32_t c0, uint32_t c1,
                                                  uint32_t wb, WarpStage &stage, Landing<MODE> &pf,
                                                  uint32_t &staged, bool &bad, bool &ovf, uint32_t &nreach,
-                                                 uint64_t &ereach, bool more, int32_t id, uint32_t GW,
-                                                 uint32_t nchunks) {
+                                                 uint64_t &ereach, bool more, int32_t id, uint32_t GW) {
   const unsigned lane = threadIdx.x & 31u;
   const uint32_t Etot = iv.edges;
   const uint32_t F = iv.count;
@@ -339,7 +475,7 @@ __device__ __forceinline__ uint32_t expand_range(const Params &p, const Interval
     else cp_async_commit();
   }
   int sb = 0, sn = kStages - 1;
-  uint32_t jn = nchunks;
+  uint32_t jn = kNoChunk;
   for (uint32_t c = c0; c < E1; c += 32u * kUnroll, ci += 32u * kUnroll) {
     if (more && lane == 0 && c + 32u * kUnroll >= E1 &&
         !(p.coop && p.kill_mode == KILL_CHUNK && doomed(ld_relaxed64(&p.ctl->kill_target), iv.epoch, id)))
@@ -355,75 +491,7 @@ __device__ __forceinline__ uint32_t expand_range(const Params &p, const Interval
       vv[u] = val[u] ? pf.col[sb][u][lane] : 0xFFFFFFFFu;
     }
 
-    if constexpr (MODE != MODE_SSSP) {
-      if (pre) {
-        uint32_t word[kUnroll];
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-          if (val[u] && vv[u] >= V) {
-            bad = true;
-            val[u] = false;
-          }
-          word[u] = val[u] ? *(p.visited + (vv[u] >> 5)) : 0xFFFFFFFFu;
-        }
-        // Row bounds of every candidate the bitmap word shows unvisited are read before
-        // its atomicOr, not after, so the two round trips overlap; a candidate that then
-        // loses the claim race wasted two cached loads.
-        int32_t ra[kUnroll], rb[kUnroll];
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-          const bool cand = val[u] && (word[u] & (1u << (vv[u] & 31u))) == 0u;
-          ra[u] = cand ? __ldg(p.row_off + vv[u]) : 0;
-          rb[u] = cand ? __ldg(p.row_off + vv[u] + 1) : 0;
-        }
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-          const uint32_t m = 1u << (vv[u] & 31u);
-          bool claim = false;
-          if (val[u] && (word[u] & m) == 0u) claim = (atomicOr(p.visited + (vv[u] >> 5), m) & m) == 0u;
-          uint32_t rs = 0u, deg = 0u;
-          bool push = false;
-          if (claim) {
-            p.level[vv[u]] = (int32_t)next_level;
-            if (ra[u] < 0 || rb[u] < ra[u] || (uint32_t)rb[u] > p.E) bad = true;
-            else {
-              rs = (uint32_t)ra[u];
-              deg = (uint32_t)(rb[u] - ra[u]);
-              push = deg > 0u;
-            }
-            nreach += 1u;
-            ereach += deg;
-          }
-          stage_push<MODE>(p, out, stage, staged, push, vv[u], rs, deg, lane);
-        }
-      } else {
-        // no pre-check: every target goes straight to its atomicOr, and only the claimed
-        // ones read their row bounds
-        bool claim[kUnroll];
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-          if (val[u] && vv[u] >= V) {
-            bad = true;
-            val[u] = false;
-          }
-          const uint32_t m = 1u << (vv[u] & 31u);
-          claim[u] = val[u] && (atomicOr(p.visited + (vv[u] >> 5), m) & m) == 0u;
-        }
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-          uint32_t rs = 0u, deg = 0u;
-          bool push = false;
-          if (claim[u]) {
-            p.level[vv[u]] = (int32_t)next_level;
-            if (row_of(p, vv[u], rs, deg)) push = deg > 0u;
-            else bad = true;
-            nreach += 1u;
-            ereach += deg;
-          }
-          stage_push<MODE>(p, out, stage, staged, push, vv[u], rs, deg, lane);
-        }
-      }
-    } else {
+    {
       // Relaxation on the packed word ds[v] = (dist << 32) | stamp.  One 64-bit atomicMin
       // with (nd << 32) | tag lowers the distance exactly when nd < dist (stamps only grow,
       // so an equal distance never rewrites the word), and the old word it returns says
@@ -488,35 +556,90 @@ __device__ __forceinline__ uint32_t expand_range(const Params &p, const Interval
   return __shfl_sync(kFull, jn, 0);
 }
 
-// Expand this warp's part of the interval.  The edge space is cut into chunks of
-// 32 * mult edges, mult in [1, kChunkUnitsMax] chosen so that small frontiers still
-// spread over every warp.  A warp's first chunk is fixed by its logical position
-// -- chunk id*NW + warp, Fig. 4's tid/stride split recomputed from the current M -- and
-// further chunks are claimed from one counter, so warps that drew cheap chunks take
-// over the rest.  The enqueue built a chunk index (entry holding each unit's first
-// edge), so a chunk starts without any search.
+__device__ __forceinline__ uint32_t round_units(uint32_t rem, uint32_t GW, uint32_t cap) {
+  return min(cap, max(1u, (rem + 2u * GW - 1u) / (2u * GW)));
+}
+
+__device__ __forceinline__ void sched_init(ChunkSched &s, uint32_t E, uint32_t GW, uint32_t cap) {
+  const bool small = E <= GW * 32u;
+  const uint32_t shift = small ? 5u : kIndexShift;
+  const uint32_t U = (E + (1u << shift) - 1u) >> shift;
+  __syncwarp();
+  if ((threadIdx.x & 31u) == 0u) {
+    s.U = U;
+    s.shift = shift;
+    s.k0 = 0u;
+    s.base = 0u;
+    s.s = small ? 1u : round_units(U, GW, cap);
+    s.cap = cap;
+  }
+  __syncwarp();
+}
+
+// The edge range [c0, c1) of chunk k (warp-uniform); false past the end of the schedule.
+// The chunk ids one warp is given only grow, so the round is advanced in place.
+__device__ __forceinline__ bool sched_chunk(ChunkSched &sc, uint32_t k, uint32_t E, uint32_t GW, uint32_t &c0,
+                                            uint32_t &c1) {
+  const uint32_t U = sc.U, shift = sc.shift;
+  uint32_t k0 = sc.k0, base = sc.base, s = sc.s;
+  bool ok = true;
+  if (k - k0 >= GW) {
+    while (k - k0 >= GW) {
+      base += GW * s;
+      if (base >= U) {
+        ok = false;
+        break;
+      }
+      k0 += GW;
+      s = round_units(U - base, GW, sc.cap);
+    }
+    __syncwarp();
+    if ((threadIdx.x & 31u) == 0u) {
+      sc.k0 = k0;
+      sc.base = base;
+      sc.s = s;
+    }
+    __syncwarp();
+  }
+  const uint32_t u0 = base + (k - k0) * s;
+  if (!ok || u0 >= U) return false;
+  c0 = u0 << shift;
+  c1 = min((u0 + s) << shift, E);
+  return true;
+}
+
+// Expand this warp's part of the interval, chunk by chunk (ChunkSched).  The enqueue
+// built a chunk index (the entry holding every kIndexEdges-th edge), so a chunk starts
+// without any search.
 template <int MODE, int NW>
 __device__ void expand(const Params &p, const Interval &iv, int32_t id, WarpStage &stage, Landing<MODE> &pf) {
   const unsigned lane = threadIdx.x & 31u;
   const uint32_t Etot = iv.edges;
   const uint32_t GW = (uint32_t)iv.M * NW;
-  const uint32_t units = (Etot + 31u) / 32u;
-  const uint32_t mult = max(1u, min(kChunkUnitsMax, (units + GW - 1u) / GW));
-  const uint32_t csize = 32u * mult;
-  const uint32_t nchunks = (units + mult - 1u) / mult;
-  uint32_t j = (uint32_t)id * NW + (threadIdx.x >> 5);
-  if (j >= nchunks) return;
+  ChunkSched &sc = pf.sched;
+  sched_init(sc, Etot, GW, MODE == MODE_SSSP ? kChunkUnitsMaxSssp : kChunkUnitsMax);
+  uint32_t c0 = 0u, c1 = 0u;
+  if (!sched_chunk(sc, (uint32_t)id * NW + (threadIdx.x >> 5), Etot, GW, c0, c1)) return;
   const uint32_t *qx = iv.sel ? p.qx[1] : p.qx[0];
   const uint32_t out = iv.sel ^ 1u;
   uint32_t staged = 0u, nreach = 0u;
+  uint32_t ch = 0u, ct = 0u;  // BFS claim ring: head and tail (warp-uniform)
   uint64_t ereach = 0ull;
   bool bad = false, ovf = false;
-  const bool more = GW < nchunks;  // chunks beyond the first M * NW are claimed from the cursor
-  while (j < nchunks) {
-    const uint32_t c0 = j * csize;
-    const uint32_t c1 = min(c0 + csize, Etot);
-    j = expand_range<MODE>(p, iv, c0, c1, qx[c0 / kIndexEdges], stage, pf, staged, bad, ovf, nreach, ereach,
-                           more, id, GW, nchunks);
+  const bool more = sc.U > GW * sc.s;  // chunks beyond round 0 are claimed from the cursor
+  for (;;) {
+    uint32_t k;
+    if constexpr (MODE == MODE_SSSP)
+      k = expand_range<MODE>(p, iv, c0, c1, qx[c0 / kIndexEdges], stage, pf, staged, bad, ovf, nreach, ereach, more,
+                             id, GW);
+    else
+      k = expand_range_bfs<MODE>(p, iv, c0, c1, qx[c0 / kIndexEdges], stage, pf, staged, bad, nreach, ereach, more,
+                                 id, GW, ch, ct);
+    if (k == kNoChunk || !sched_chunk(sc, k, Etot, GW, c0, c1)) break;
+  }
+  if constexpr (MODE != MODE_SSSP) {
+    if (ct != ch) claim_batch(p, out, stage, staged, pf.cand, ch, ct - ch, (uint32_t)iv.level + 1u, bad, nreach,
+                              ereach, lane);
   }
   if (staged) stage_flush<MODE>(p, out, stage, staged, lane);
   // this warp's newly reached vertices and their out-edges (the TEPS numerator)

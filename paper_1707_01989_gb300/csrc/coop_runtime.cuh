@@ -53,8 +53,10 @@ constexpr int kTraverseSmemMin = 56 * 1024;
 constexpr int kCorunnerSmem = 176 * 1024;
 static_assert(kTraverseSmemMin + kCorunnerSmem + 2 * 1024 > 228 * 1024, "co-runner must not fit beside a traversal CTA");
 constexpr uint64_t kEntryGatherNs = 20000;  // master waits this long for its launch to register
-constexpr uint32_t kIndexEdges = 128;       // granularity of the chunk index (edges per unit)
-constexpr uint32_t kChunkUnitsMax = 16;     // a work chunk spans 1..16 32-edge units, sized to the frontier
+constexpr uint32_t kIndexShift = 7;
+constexpr uint32_t kIndexEdges = 1u << kIndexShift;  // granularity of the chunk index (edges per unit)
+constexpr uint32_t kChunkUnitsMax = 16;     // a chunk of a wide BFS level spans 1..16 units of kIndexEdges edges
+constexpr uint32_t kChunkUnitsMaxSssp = 4;  // SSSP: 1..4 units
 // A claim reads the target's state (visited bit, distance) before its atomic on frontiers
 // of at least kPrecheckEdges edges, where the read saves most atomics (claim atomics in
 // bulk are far slower than loads).  On smaller frontiers the read is one more dependent

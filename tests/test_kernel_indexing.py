@@ -1,8 +1,9 @@
 """Host emulation of the expansion kernel's warp-level index arithmetic.
 
-The persistent kernel cuts a frontier's edge space into CHUNK-edge chunks; the
-enqueue records, for every chunk boundary, the queue slot of the entry holding it
-(the chunk index).  A warp expanding a chunk starts a 32-entry window of frontier
+The persistent kernel cuts a frontier's edge space into chunks (ChunkSched: one 32-edge
+chunk per warp on small frontiers, else rounds of chunks of 1..cap 128-edge units, each
+round about half of what is left); the enqueue records, for every 128-edge boundary,
+the queue slot of the entry holding it (the chunk index).  A warp expanding a chunk starts a 32-entry window of frontier
 entries at that slot and maps each lane to one edge with a ballot over ended entries,
 a __reduce_or of start bits and a popc over lanemask_le.  This test replays exactly
 that arithmetic in numpy (one vector = one warp) over random frontiers and checks that
@@ -50,7 +51,67 @@ def load(qo, qs, F, Etot, i):
     return MAXU, MAXU, 0
 
 
-CHUNK = 128  # the index granularity (kIndexEdges); chunks are 1..8 units
+CHUNK = 128  # the index granularity (kIndexEdges)
+CAP_BFS, CAP_SSSP = 16, 4  # kChunkUnitsMax, kChunkUnitsMaxSssp: units per chunk at most
+
+
+def round_units(rem, gw, cap):
+    return min(cap, max(1, (rem + 2 * gw - 1) // (2 * gw)))
+
+
+class Sched:
+    """ChunkSched of one warp: sched_init, then sched_chunk for growing chunk ids."""
+
+    def __init__(self, E, gw, cap):
+        small = E <= gw * 32
+        self.E, self.gw, self.cap = E, gw, cap
+        self.shift = 5 if small else 7
+        self.U = (E + (1 << self.shift) - 1) >> self.shift
+        self.k0, self.base = 0, 0
+        self.s = 1 if small else round_units(self.U, gw, cap)
+
+    def more(self):
+        return self.U > self.gw * self.s
+
+    def chunk(self, k):
+        k0, base, s = self.k0, self.base, self.s
+        ok = True
+        while k - k0 >= self.gw:
+            base += self.gw * s
+            assert base < 1 << 32
+            if base >= self.U:
+                ok = False
+                break
+            k0 += self.gw
+            s = round_units(self.U - base, self.gw, self.cap)
+        self.k0, self.base, self.s = k0, base, s
+        u0 = base + (k - k0) * s
+        if not ok or u0 >= self.U:
+            return None
+        return u0 << self.shift, min((u0 + s) << self.shift, self.E)
+
+
+def schedule_chunks(E, gw, cap, rng):
+    """Every chunk the warps of one interval expand, in a random interleaving of their
+    cursor claims: round 0's chunk w is warp w's, later ids come from one counter."""
+    warps = [Sched(E, gw, cap) for _ in range(gw)]
+    more = warps[0].more()
+    out, live, cursor = [], [], 0
+    for w in range(gw):
+        r = warps[w].chunk(w)
+        if r is not None:
+            out.append(r)
+            live.append(w)
+    while more and live:
+        i = int(rng.integers(0, len(live)))
+        w = live[i]
+        r = warps[w].chunk(gw + cursor)
+        cursor += 1
+        if r is None:
+            live.pop(i)
+        else:
+            out.append(r)
+    return out, more
 
 
 def index_chunks(qo, degs, nchunks):
@@ -118,16 +179,18 @@ def check_frontier_chunks(degs, rng):
     qx = index_chunks(qo, degs, nchunks)
     assert np.all(qx >= 0)
     assert np.array_equal(qx, owner[np.arange(nchunks) * CHUNK])
-    for mult in (1, 3, 8, 16):  # chunks of 32*mult edges, started from the 128-edge index
-        units = (Etot + 31) // 32
-        seen = np.zeros(Etot, dtype=np.int64)
-        for j in rng.permutation((units + mult - 1) // mult):
-            c0, c1 = j * 32 * mult, min((j + 1) * 32 * mult, Etot)
-            for e, pos in emulate_warp(qo, qs, F, Etot, c0, c1, wb=int(qx[c0 // CHUNK])):
-                u = owner[e]
-                assert pos == qs[u] + (e - qo[u])
-                seen[e] += 1
-        assert np.all(seen == 1)
+    for gw in (1, 3, 8, 31, 64, 4712):  # warps of the interval (M * NW)
+        for cap in (CAP_BFS, CAP_SSSP):
+            seen = np.zeros(Etot, dtype=np.int64)
+            chunks, _ = schedule_chunks(Etot, gw, cap, rng)
+            for c0, c1 in chunks:
+                if Etot > gw * 32:  # wide frontier: indexed starts, at most cap units
+                    assert c0 % CHUNK == 0 and c1 - c0 <= cap * CHUNK
+                for e, pos in emulate_warp(qo, qs, F, Etot, c0, c1, wb=int(qx[c0 // CHUNK])):
+                    u = owner[e]
+                    assert pos == qs[u] + (e - qo[u])
+                    seen[e] += 1
+            assert np.all(seen == 1)
 
 
 @pytest.mark.parametrize("seed", range(12))
@@ -142,6 +205,63 @@ def test_chunk_index_random_frontiers(seed):
         degs = rng.integers(1, 20, size=F)
         degs[rng.integers(0, F)] = 3 * CHUNK + 17   # a hub spanning several chunks
     check_frontier_chunks(degs.astype(np.int64), rng)
+
+
+@pytest.mark.parametrize("E", [1, 31, 32, 33, 127, 128, 129, 4095, 150784, 150785, 300000, 36508052, 27740094,
+                               (1 << 31) - 1])
+@pytest.mark.parametrize("gw", [1, 2, 31, 4712, 63488])
+def test_chunk_schedule_covers_the_edge_space_once(E, gw):
+    """The chunk ranges of ChunkSched tile [0, E) exactly, whatever order the cursor's ids
+    reach the warps in; each round takes about half of what is left; the counts stay in
+    32 bits.  (R-MAT 22's two wide BFS levels are among the sizes.)"""
+    rng = np.random.default_rng(E % 1000 + gw)
+    for cap in (CAP_BFS, CAP_SSSP):
+        if E > 50_000_000 and (gw < 31 or cap == CAP_SSSP):
+            continue  # the emulation walks every chunk: keep the host time small
+        chunks, more = schedule_chunks(E, gw, cap, rng)
+        chunks.sort()
+        assert chunks[0][0] == 0 and chunks[-1][1] == E
+        for (a0, a1), (b0, b1) in zip(chunks, chunks[1:]):
+            assert a1 == b0 and a0 < a1
+        if E <= gw * 32:
+            assert not more and len(chunks) == (E + 31) // 32 and all(c1 - c0 <= 32 for c0, c1 in chunks)
+        else:
+            assert all(c0 % CHUNK == 0 and c1 - c0 <= cap * CHUNK for c0, c1 in chunks)
+
+
+def test_chunk_schedule_shrinks_towards_the_end():
+    """R-MAT 22's first wide level with 152 CTAs of 31 warps: most edges go in chunks of
+    the cap, the last chunks are single 128-edge units, and there are far fewer chunk
+    starts than with fixed 512-edge chunks."""
+    E, gw = 36508052, 152 * 31
+    chunks, _ = schedule_chunks(E, gw, CAP_BFS, np.random.default_rng(1))
+    sizes = np.array(sorted(chunks))[:, 1] - np.array(sorted(chunks))[:, 0]
+    assert sizes[0] == CAP_BFS * CHUNK and sizes[-2] == CHUNK
+    big = sizes[sizes == CAP_BFS * CHUNK].sum()
+    assert big > 0.5 * E
+    assert len(chunks) < (E + 511) // 512 / 2
+
+
+def test_claim_ring_never_overwrites_a_pending_candidate():
+    """The BFS claim ring (kCand = 64 slots): after every 32-edge group at most 32 new
+    candidates arrive, and 32 are claimed whenever 32 or more are pending, so no slot is
+    rewritten while it still holds a pending candidate."""
+    rng = np.random.default_rng(9)
+    ring = [None] * 64
+    ch = ct = 0
+    for _ in range(20000):
+        n = int(rng.integers(0, 33)) if rng.random() < 0.3 else int(rng.integers(0, 4))
+        for i in range(n):
+            slot = (ct + i) & 63
+            assert ring[slot] is None, "a pending candidate would be overwritten"
+            ring[slot] = ct + i
+        ct += n
+        if ct - ch >= 32:
+            for i in range(32):
+                assert ring[(ch + i) & 63] == ch + i
+                ring[(ch + i) & 63] = None
+            ch += 32
+        assert ct - ch <= 63
 
 
 def check_frontier(degs, n_warps, rng):
