@@ -1,25 +1,28 @@
 #!/usr/bin/env python3
-"""Benchmark: cooperative frontier SSSP on an R-MAT scale-20 graph (one GB300).
+"""Benchmark: cooperative BFS on an R-MAT scale-22 graph (one GB300).
 
-Workload (the headline configuration): directed R-MAT, scale 20, edge factor 16,
-a/b/c/d = 0.57/0.19/0.19/0.05, seed 20, self-loops and duplicates removed; uint32
-weights uniform in [1, 255] (seed 21); source = highest out-degree vertex.  One step
-= one complete traversal (init kernel + persistent cooperative kernel) with the graph
-already resident in HBM.  value = GTEPS = E_s / t, E_s = out-edges of reached vertices.
+Workload (the headline configuration, the largest single-GPU graph of the measurement
+plan and the one the HBM-roofline target is stated on): directed R-MAT, scale 22, edge
+factor 16, a/b/c/d = 0.57/0.19/0.19/0.05, seed 22, self-loops and duplicates removed;
+source = highest out-degree vertex.  One step = one complete traversal (init kernel +
+persistent cooperative kernel, its scheduler polling for offer_kill / request_fork) with
+the graph already resident in HBM.  value = GTEPS = E_s / t, E_s = out-edges of reached
+vertices.
 
 Also on the same JSON line: the roofline of the persistent kernel (algorithmic bytes
-4V + 24 V_r + 12 E_s per launch over its CUDA-event duration against the measured HBM
-copy bandwidth), the end-to-end number through the C ABI with host buffers (H2D of
-the CSR and weights, D2H of the distances inside the timed region), the CPU oracle
-timed on this host, clock samples taken during the timed region, and secondary
-figures (skipped with --no-extras): BFS on R-MAT scale 22 with the non-cooperative
+4V + 20 V_r + 8 E_s per launch over its CUDA-event duration against the measured HBM
+copy bandwidth), the end-to-end number through the C ABI with host buffers (H2D of the
+CSR, D2H of the levels inside the timed region), the CPU oracle timed on this host,
+clock samples taken during the timed region, parity of the last timed step's output
+against the oracle, and secondary figures (skipped with --no-extras): frontier SSSP on
+R-MAT scale 20 with its own roofline, e2e and oracle baseline, the non-cooperative
 baseline's overhead ratio and random kill/fork schedules, the co-runner (fp32 saxpy on
 half the SMs every 16.7 ms) with and without cooperation, gather time under each kill
 mode, the topology-driven SSSP, the work-stealing octree, the batched and served forms,
 the 256x256 grid BFS (barrier-latency bound) and empty-barrier latency.
 
---impl reference times the CPU oracle (binary-heap Dijkstra, one core) on the same
-workload: the slow reference arm.
+--impl reference times the CPU oracle (FIFO-queue BFS, one core) on the same workload:
+the slow reference arm.
 
 Multi-GPU (--gpus N under torchrun): replicas only -- every rank runs the same
 workload on its own GPU; value = all ranks' edges / the slowest rank's time.
@@ -42,8 +45,8 @@ sys.path.insert(0, ROOT)
 METRIC = "BFS/SSSP GTEPS (1 GB300, % HBM roofline); barrier us; co-runner p99 latency"
 WORKLOADS = {
     # name: (graph kind, scale, graph seed, weight seed, traversal)
-    "rmat20-sssp": ("rmat", 20, 20, 21, "sssp"),   # the headline configuration
-    "rmat22-bfs": ("rmat", 22, 22, None, "bfs"),
+    "rmat22-bfs": ("rmat", 22, 22, None, "bfs"),    # the headline configuration
+    "rmat20-sssp": ("rmat", 20, 20, 21, "sssp"),
     "grid256-bfs": ("grid", 256, None, None, "bfs"),
 }
 
@@ -128,7 +131,10 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def load_workload(name="rmat20-sssp"):
+HEADLINE = "rmat22-bfs"
+
+
+def load_workload(name=HEADLINE):
     """(graph, weights or None, source, traversal) of a named workload."""
     import graphgen as gg
     kind, scale, seed, wseed, trav = WORKLOADS[name]
@@ -187,6 +193,129 @@ def config_of(name, g, extra=None):
     return c
 
 
+def measure(coop, ctx, dev, stream, flush, name, steps, warmup, world=1, cpu_budget=None, clocks=None):
+    """One workload's figures: device-timed GTEPS over `steps` traversals (L2 flushed
+    between them, inputs resident), the persistent kernel's roofline, the end-to-end rate
+    through the C ABI with the inputs copied from pinned host memory and the result copied
+    back inside the timed region, parity of the last timed step's output against the
+    oracle, and (cpu_budget given) the oracle timed on one host core.  `clocks` (a
+    ClockSampler) samples the SM clock during the device-timed steps."""
+    import contextlib
+    import numpy as np
+    import torch
+    g, w, src, trav = load_workload(name)
+    V, E = g.num_vertices, g.num_edges
+    ro_h = torch.from_numpy(np.array(g.row_off)).pin_memory()
+    col_h = torch.from_numpy(np.array(g.col)).pin_memory()
+    w_h = torch.from_numpy(w.view(np.int32)).pin_memory() if w is not None else None
+    ro, col = ro_h.to(dev), col_h.to(dev)
+    wt = w_h.to(dev) if w_h is not None else None
+    out_d = torch.empty(V, dtype=torch.int32, device=dev)
+    out_h = torch.empty(V, dtype=torch.int32).pin_memory()
+    csr = coop.make_csr(ro, col)
+    threads = coop.coop_query(ctx)["threads_per_cta"]
+
+    if trav == "sssp":
+        def step():
+            coop.coop_sssp(ctx, csr, wt, src, out_d, stream=stream)
+    else:
+        def step():
+            coop.coop_bfs(ctx, csr, src, out_d, stream=stream)
+
+    def result():
+        r = out_d.cpu().numpy()
+        return r.view(np.uint32) if trav == "sssp" else r
+
+    for _ in range(warmup):
+        step()
+    stream.synchronize()
+    st = coop.coop_get_stats(ctx)
+    vr, es = reached_work(g, reached_of(result(), trav))
+    out_d.fill_(-2)  # the timed steps must write every element again
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.barrier()
+    torch.cuda.synchronize(dev)
+    step_ms, kern_us = [], []
+    with (clocks if clocks is not None else contextlib.nullcontext()):
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            kern_us.append(coop.coop_get_stats(ctx).kernel_us)
+    torch.cuda.synchronize(dev)
+    last = result()  # the last timed step's output, checked against the oracle below
+    t_step = job_time(statistics.mean(step_ms) / 1e3, world, dev)
+    value = whole_job_rate(es, world, t_step)
+
+    # roofline of the dominant kernel (the persistent traversal kernel)
+    hbm, peak_kind = peaks()
+    B = algorithmic_bytes(V, vr, es, trav)
+    k_s = statistics.mean(kern_us) / 1e6
+    achieved = B / k_s / 1e9
+    traffic = None
+    tr = TRAFFIC.get(name)
+    if tr and tr.get("sources_sha") == sources_sha():
+        traffic = tr["bytes"]
+
+    # end to end through the C ABI with host buffers: H2D inputs, traversal, D2H result
+    h2d = (V + 1) * 4 + E * 4 + (E * 4 if wt is not None else 0)
+    d2h = V * 4
+    e2e_ms = []
+    for i in range(warmup + steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            ro.copy_(ro_h, non_blocking=True)
+            col.copy_(col_h, non_blocking=True)
+            if wt is not None:
+                wt.copy_(w_h, non_blocking=True)
+        step()
+        with torch.cuda.stream(stream):
+            out_h.copy_(out_d, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_val = whole_job_rate(es, world, job_time(statistics.mean(e2e_ms) / 1e3, world, dev))
+    e2e_out = out_h.numpy().view(np.uint32) if trav == "sssp" else out_h.numpy()
+
+    res = {
+        "value": round(value, 4), "ms_per_step": round(t_step * 1e3, 4),
+        "dtype": "u32" if trav == "sssp" else "int32",
+        "config": config_of(name, g, {
+            "V_reached": vr, "E_s": es, "source": src, "parallelism": "replicas",
+            "l2": "flushed between steps (512 MB write)", "ctas": st.max_active, "threads_per_cta": threads}),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4), "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": f"coop_traverse<{trav.upper()}>", "kernel_us": round(k_s * 1e6, 2),
+                     "algorithmic_bytes": B},
+        "e2e": {"value": round(e2e_val, 4), "unit": "GTEPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "stats": {"levels": st.levels, "barriers": st.barriers, "frontier_total": st.frontier_total,
+                  "edges_expanded": st.edges_scanned, "work_inflation": round(st.edges_scanned / max(es, 1), 3)},
+    }
+    if cpu_budget is not None:
+        ref, times = time_cpu_oracle(g, w, src, trav, budget_s=cpu_budget)
+        res["parity_last_step"] = bool(np.array_equal(ref, last)) and bool(np.array_equal(ref, e2e_out))
+        algo = "binary-heap Dijkstra" if trav == "sssp" else "FIFO-queue BFS"
+        res["cpu_baseline"] = {
+            "value": round(es / statistics.mean(times) / 1e9, 6), "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"{len(times)} full {algo} traversal(s) of the {name} workload on 1 host core "
+                      f"({os.cpu_count()} cores present)"}
+    res["_graph"] = (g, src, ro, col, csr)  # reused by the secondary figures on the same graph
+    return res
+
+
 def job_time(t_local: float, world: int, device) -> float:
     """Seconds of the whole job: the slowest rank's time (MAX all-reduce, then a barrier)."""
     if world <= 1:
@@ -240,7 +369,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat20-sssp", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=HEADLINE, choices=sorted(WORKLOADS))
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--extras", default="all",
                     help="comma-separated secondary figures to run (default all): " + ", ".join(EXTRAS))
@@ -266,136 +395,42 @@ def main():
     dev = torch.device("cuda", local)
     args.warmup = max(3, args.warmup)
 
-    g, w, src, trav = load_workload(args.workload)
-    V, E = g.num_vertices, g.num_edges
-    ro_h = torch.from_numpy(np.array(g.row_off)).pin_memory()
-    col_h = torch.from_numpy(np.array(g.col)).pin_memory()
-    w_h = torch.from_numpy(w.view(np.int32)).pin_memory() if w is not None else None
-    ro, col = ro_h.to(dev), col_h.to(dev)
-    wt = w_h.to(dev) if w_h is not None else None
-    out_d = torch.empty(V, dtype=torch.int32, device=dev)
-    out_h = torch.empty(V, dtype=torch.int32).pin_memory()
-    csr = coop.make_csr(ro, col)
     ctx = coop.coop_init(local, 0, args.threads)
     coop.coop_set_timing(ctx, True)
-    threads = coop.coop_query(ctx)["threads_per_cta"]
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
-
-    if trav == "sssp":
-        def step():
-            coop.coop_sssp(ctx, csr, wt, src, out_d, stream=stream)
-    else:
-        def step():
-            coop.coop_bfs(ctx, csr, src, out_d, stream=stream)
-
-    for _ in range(args.warmup):
-        step()
-    stream.synchronize()
-    st = coop.coop_get_stats(ctx)
-    res = out_d.cpu().numpy()
-    if trav == "sssp":
-        res = res.view(np.uint32)
-    vr, es = reached_work(g, reached_of(res, trav))
-
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    step_ms, kern_us = [], []
-    with ClockSampler(local) as clocks:
-        for _ in range(args.steps):
-            flush.zero_()
-            torch.cuda.synchronize(dev)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            step()
-            e1.record(stream)
-            e1.synchronize()
-            step_ms.append(e0.elapsed_time(e1))
-            kern_us.append(coop.coop_get_stats(ctx).kernel_us)
-    torch.cuda.synchronize(dev)
-    t_step = job_time(statistics.mean(step_ms) / 1e3, world, dev)
-    value = whole_job_rate(es, world, t_step)
-
-    # roofline of the dominant kernel (the persistent traversal kernel)
-    hbm, peak_kind = peaks()
-    B = algorithmic_bytes(V, vr, es, trav)
-    k_s = statistics.mean(kern_us) / 1e6
-    achieved = B / k_s / 1e9
-    traffic = None
-    tr = TRAFFIC.get(args.workload)
-    if tr and tr.get("sources_sha") == sources_sha():
-        traffic = tr["bytes"]
-
-    # end to end through the C ABI with host buffers: H2D inputs, traversal, D2H result
-    h2d = (V + 1) * 4 + E * 4 + (E * 4 if wt is not None else 0)
-    d2h = V * 4
-    e2e_ms = []
-    for i in range(args.warmup + args.steps):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        flush.zero_()
-        torch.cuda.synchronize(dev)
-        e0.record(stream)
-        with torch.cuda.stream(stream):
-            ro.copy_(ro_h, non_blocking=True)
-            col.copy_(col_h, non_blocking=True)
-            if wt is not None:
-                wt.copy_(w_h, non_blocking=True)
-        step()
-        with torch.cuda.stream(stream):
-            out_h.copy_(out_d, non_blocking=True)
-        e1.record(stream)
-        e1.synchronize()
-        if i >= args.warmup:
-            e2e_ms.append(e0.elapsed_time(e1))
-    e2e_val = whole_job_rate(es, world, job_time(statistics.mean(e2e_ms) / 1e3, world, dev))
-
+    clocks = ClockSampler(local)
+    m = measure(coop, ctx, dev, stream, flush, args.workload, args.steps, args.warmup, world,
+                args.cpu_budget if rank == 0 else None, clocks)
     if rank == 0:
         extras = {}
         if not args.no_extras:
-            extras = secondary(coop, ctx, dev, stream, flush, args)
-        ref, times = time_cpu_oracle(g, w, src, trav, budget_s=args.cpu_budget)
-        extras["parity_vs_oracle"] = bool(np.array_equal(ref, res))
-        algo = "binary-heap Dijkstra" if trav == "sssp" else "FIFO-queue BFS"
-        cpu = {"value": round(es / statistics.mean(times) / 1e9, 6), "unit": "GTEPS", "cores": 1, "kind": "oracle",
-               "sample": f"{len(times)} full {algo} traversal(s) of the {args.workload} workload on 1 host core "
-                         f"({os.cpu_count()} cores present)"}
+            extras = secondary(coop, ctx, dev, stream, flush, args, m)
+        extras["parity_vs_oracle"] = m["parity_last_step"]
         line = {
-            "metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(t_step * 1e3, 4), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32" if trav == "sssp" else "int32",
-            "data": "synthetic",
-            "config": config_of(args.workload, g, {
-                "V_reached": vr, "E_s": es, "source": src, "parallelism": "replicas",
-                "l2": "flushed between steps (512 MB write)", "ctas": st.max_active, "threads_per_cta": threads}),
-            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                         "frac": round(achieved / hbm, 4), "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": f"coop_traverse<{trav.upper()}>", "kernel_us": round(k_s * 1e6, 2),
-                         "algorithmic_bytes": B},
-            "e2e": {"value": round(e2e_val, 4), "unit": "GTEPS", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
-            "gpu_launches": 2 * args.steps,
-            "clocks": clocks.summary(),
-            "cpu_baseline": cpu,
-            "stats": {"levels": st.levels, "barriers": st.barriers, "frontier_total": st.frontier_total,
-                      "edges_expanded": st.edges_scanned, "work_inflation": round(st.edges_scanned / max(es, 1), 3)},
-            "extras": extras,
+            "metric": METRIC, "value": m["value"], "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": m["dtype"], "data": "synthetic",
+            "config": m["config"], "roofline": m["roofline"], "e2e": m["e2e"],
+            "gpu_launches": 2 * args.steps, "clocks": clocks.summary(), "cpu_baseline": m["cpu_baseline"],
+            "stats": m["stats"], "extras": extras,
         }
         print(json.dumps(line), flush=True)
+    m.pop("_graph", None)
     coop.coop_destroy(ctx)
     if world > 1:
         dist.destroy_process_group()
     return 0
 
 
-def random_schedules(coop, ctx, csr, src, lv, ref, stream, es, seeds=(0, 1, 2, 3)):
-    """R-MAT 22 BFS under seeded random kill/fork schedules: bit-exact flag and throughput."""
+def random_schedules(coop, ctx, csr, src, lv, ref, stream, es, seeds=(0, 1, 2, 3), p_kill=0.5, p_fork=1.0):
+    """R-MAT 22 BFS under seeded random kill/fork schedules: bit-exact flag and throughput.
+    With these probabilities every seed both kills and forks within the graph's five
+    resizing barriers."""
     import numpy as np
     res = []
     for seed in seeds:
-        coop.coop_set_schedule(ctx, seed, 0.3, 0.5)
+        coop.coop_set_schedule(ctx, seed, p_kill, p_fork)
         t0 = time.perf_counter()
         st = coop.coop_bfs(ctx, csr, src, lv, stream=stream, stats=True)
         dt = time.perf_counter() - t0
@@ -930,8 +965,8 @@ def serving(coop, dev, n_graphs=32, rate=200.0, duration_s=3.0, slots=4, budget=
             "all_ok": all(r.status == 0 for r in done)}
 
 
-EXTRAS = ("bfs_rmat22", "grid_bfs", "preemption", "gather_by_kill_mode", "topology_driven_sssp", "octree",
-          "batched", "serving", "barrier_us")
+EXTRAS = ("sssp_rmat20", "bfs_rmat22", "grid_bfs", "preemption", "gather_by_kill_mode", "topology_driven_sssp",
+          "octree", "batched", "serving", "barrier_us")
 
 
 def selected_extras(spec: str):
@@ -945,10 +980,12 @@ def selected_extras(spec: str):
     return tuple(x for x in EXTRAS if x in names)
 
 
-def secondary(coop, ctx, dev, stream, flush, args):
-    """BFS on R-MAT 22, grid BFS, the co-runner with and without cooperation, batching,
-    serving, barrier latency and the non-cooperative baseline ratio.  Each part runs on
-    its own: one that fails records its error under its key and the others still run."""
+def secondary(coop, ctx, dev, stream, flush, args, head):
+    """SSSP on R-MAT 20 (with its own roofline, e2e and oracle baseline), the R-MAT 22
+    BFS's non-cooperative baseline ratio, kill/fork schedules and co-runner, grid BFS, the
+    co-runner with and without cooperation, batching, serving and barrier latency.  Each
+    part runs on its own: one that fails records its error under its key and the others
+    still run.  `head` is the headline measurement (its graph is reused)."""
     import traceback
     import numpy as np
     import torch
@@ -989,14 +1026,25 @@ def secondary(coop, ctx, dev, stream, flush, args):
 
     hbm, _ = peaks()
 
+    def sssp_rmat20():
+        # frontier SSSP on R-MAT scale 20: the full set of figures of the headline
+        m = measure(coop, ctx, dev, stream, flush, "rmat20-sssp", max(3, args.steps), args.warmup, 1,
+                    min(args.cpu_budget, 10.0))
+        m.pop("_graph", None)
+        m["parity_vs_oracle"] = m.pop("parity_last_step")
+        return m
+
     def rmat22():
-        # BFS on R-MAT scale 22, its schedules and the co-runner on it
-        g = gg.rmat(22, 16, seed=22)
-        src = gg.max_out_degree_vertex(g)
-        ro = torch.from_numpy(np.array(g.row_off)).to(dev)
-        col = torch.from_numpy(np.array(g.col)).to(dev)
+        # BFS on R-MAT scale 22: the non-cooperative baseline, schedules and the co-runner
+        if args.workload == "rmat22-bfs":
+            g, src, ro, col, csr = head["_graph"]
+        else:
+            g = gg.rmat(22, 16, seed=22)
+            src = gg.max_out_degree_vertex(g)
+            ro = torch.from_numpy(np.array(g.row_off)).to(dev)
+            col = torch.from_numpy(np.array(g.col)).to(dev)
+            csr = coop.make_csr(ro, col)
         lv = torch.empty(g.num_vertices, dtype=torch.int32, device=dev)
-        csr = coop.make_csr(ro, col)
         f = lambda: coop.coop_bfs(ctx, csr, src, lv, stream=stream)
         for _ in range(3):
             f()
@@ -1056,6 +1104,7 @@ def secondary(coop, ctx, dev, stream, flush, args):
         return res
 
     parts = {
+        "sssp_rmat20": lambda: guarded("sssp_rmat20", sssp_rmat20),
         "bfs_rmat22": lambda: guarded(None, rmat22, "bfs_rmat22"),
         "grid_bfs": lambda: guarded("grid_bfs", grid),
         "preemption": lambda: guarded("preemption", lambda: preemption(coop, ctx, dev, stream)),

@@ -324,16 +324,21 @@ def test_topology_driven_sssp_heavy_rows_under_schedules(ctx, seed):
 
 
 @pytest.mark.slow
-def test_full_size_rmat22_bfs_under_a_schedule(ctx):
-    """R-MAT scale 22 BFS (the cooperative-multitasking workload) under a forced random
-    kill/fork schedule: bit-exact levels and a legal resize log."""
+def test_full_size_rmat22_bfs_under_schedules(ctx):
+    """R-MAT scale 22 BFS (the cooperative-multitasking workload) under the bench's forced
+    random kill/fork schedules: every seed kills and forks, the levels are bit-exact and
+    the resize log is legal."""
+    from schedule_model import RMAT22_SCHEDULE, RMAT22_SEEDS
     g = gg.rmat(22, 16, seed=22)
     src = gg.max_out_degree_vertex(g)
-    coop.coop_set_schedule(ctx, 3, p_kill=0.3, p_fork=0.5)  # the bench's seed 3: kills and forks
-    try:
-        lv, st = run_bfs(ctx, DevGraph(g), src)
-    finally:
-        coop.coop_set_schedule(ctx, 0, 0.0, 0.0)
-    assert_same(lv, oracle.bfs(g, src), "rmat22 bfs under a schedule")
-    assert st.kills > 0 and st.forks > 0
-    _replay(ctx, st)
+    dg = DevGraph(g)
+    ref = oracle.bfs(g, src)
+    for seed in RMAT22_SEEDS:
+        coop.coop_set_schedule(ctx, seed, *RMAT22_SCHEDULE)
+        try:
+            lv, st = run_bfs(ctx, dg, src)
+        finally:
+            coop.coop_set_schedule(ctx, 0, 0.0, 0.0)
+        assert_same(lv, ref, f"rmat22 bfs under schedule {seed}")
+        assert st.kills > 0 and st.forks > 0, (seed, st.kills, st.forks)
+        _replay(ctx, st)

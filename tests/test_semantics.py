@@ -133,3 +133,24 @@ def test_schedule_invariance_sssp_model(seed):
     src = gg.max_out_degree_vertex(g)
     d, _ = cooperative_sssp_model(g, w, src, 4, 2, _random_schedule(100 + seed))
     np.testing.assert_array_equal(np.array(d, dtype=np.uint64), oracle.dijkstra(g, w, src))
+
+
+def test_rmat22_bench_schedules_both_kill_and_fork():
+    """Every seeded schedule the bench and the full-size GPU test run on R-MAT 22 kills
+    and forks within its five resizing barriers (model of the releaser's draws with the
+    GPU's 152 CTAs), and never drops below the master CTA."""
+    from schedule_model import RMAT22_RESIZING_BARRIERS, RMAT22_SCHEDULE, RMAT22_SEEDS, simulate
+    for seed in RMAT22_SEEDS:
+        kills, forks, spawned, M = simulate(seed, *RMAT22_SCHEDULE, 152, RMAT22_RESIZING_BARRIERS)
+        assert kills > 0 and forks > 0 and spawned >= forks and 1 <= M <= 152, seed
+
+
+def test_schedule_model_reproduces_the_earlier_fork_free_seeds():
+    """The model against recorded device runs: with p_kill 0.3 and p_fork 0.5 on R-MAT 22,
+    seeds 0, 1 and 2 recorded kills but no forks, seed 0 ending on the master CTA alone,
+    and seed 3 recorded both."""
+    from schedule_model import simulate
+    runs = [simulate(s, 0.3, 0.5, 152, 5) for s in range(4)]
+    assert all(k > 0 and f == 0 for k, f, _, _ in runs[:3])
+    assert runs[0][3] == 1
+    assert runs[3][0] > 0 and runs[3][1] > 0
