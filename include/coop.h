@@ -75,7 +75,8 @@ typedef struct {
 
 /* What one traversal did (all counters cover the whole run). */
 typedef struct {
-    int32_t levels;         /* frontier rounds expanded (BFS levels; SSSP rounds) */
+    int32_t levels;         /* frontier rounds expanded (BFS levels; SSSP rounds, each a select
+                               and an expand interval, so barriers = 2 x levels) */
     int32_t barriers;       /* resizing barriers passed, excluding the entry one */
     int32_t kills;          /* CTAs that left through offer_kill */
     int32_t forks;          /* CTAs that joined through request_fork after entry */
@@ -85,8 +86,9 @@ typedef struct {
     int32_t status;         /* coop_status of the run */
     int32_t ctas_launched;  /* CTAs launched for the run: main grid + every forked CTA */
     int32_t reserved;
-    int64_t edges_scanned;  /* sum of out-degrees over every frontier (BFS: E_s) */
-    int64_t frontier_total; /* sum of frontier sizes */
+    int64_t edges_scanned;  /* sum of out-degrees over every expanded frontier (BFS: E_s;
+                               SSSP: over the near queues, E_s x work inflation) */
+    int64_t frontier_total; /* sum of expanded frontier sizes */
     int64_t vertices_reached; /* V_r: vertices reached from the source (incl. it) */
     int64_t reached_edges;  /* E_s: out-edges of the reached vertices (the TEPS numerator) */
     double gather_us_max;   /* longest coop_request_resources wait during the run */
@@ -115,8 +117,12 @@ coop_status coop_bfs(coop_ctx *ctx, const coop_csr *g, int32_t source, int32_t *
                      coop_stream stream, coop_stats *stats);
 
 /*
- * Frontier single-source shortest paths (Table 1 "l-sssp", read as data-driven
- * Bellman-Ford): d_dist[v] = least total weight of a path source -> v, 0xFFFFFFFF if
+ * Frontier single-source shortest paths (Table 1 "l-sssp": two resizing barriers per
+ * iteration, read as data-driven Bellman-Ford in rounds): each round's first interval
+ * selects the pending vertices of lowest tentative distance (enough out-edges to keep
+ * the GPU busy, all of them if fewer) and defers the rest; its second relaxes the
+ * selected vertices' out-edges, and every vertex whose distance drops is pending for the
+ * next round.  d_dist[v] = least total weight of a path source -> v, 0xFFFFFFFF if
  * unreachable (uint32[V], device); d_weights is uint32[E] (device).  Every shortest
  * distance must fit below 2^32 - 1, else the run reports COOP_EOVERFLOW.
  * Asynchronous unless stats is non-NULL (as coop_bfs).

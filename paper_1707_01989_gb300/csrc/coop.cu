@@ -100,6 +100,14 @@ constexpr int kStage = 64;
 constexpr uint32_t kCand = 64;
 constexpr uint32_t kNoChunk = 0xFFFFFFFFu;  // no further chunk for this warp
 
+// Queue q (0, 1 or 2) of a per-queue pointer array of the kernel parameters, chosen by
+// selects: an index into the parameter array itself would make the compiler copy it to
+// local memory.
+template <typename T>
+__device__ __forceinline__ T *queue(T *const (&a)[3], uint32_t q) {
+  return q == 0u ? a[0] : q == 1u ? a[1] : a[2];
+}
+
 // The chunk schedule of one interval.  A frontier of at most GW * 32 edges (GW = M * NW
 // worker warps) gets one 32-edge chunk per warp.  A larger one is cut into units of
 // kIndexEdges edges, handed out in rounds of GW chunks: round r's chunks span
@@ -119,9 +127,22 @@ struct ChunkSched {  // per warp, in shared memory: touched only between chunks
 };
 
 // Chunk index: for every unit boundary j*kIndexEdges inside an entry's edge range
-// [o, o + d), record the entry's queue slot.
-__device__ __forceinline__ void index_chunks(uint32_t *qx, uint32_t o, uint32_t d, uint32_t slot) {
-  for (uint32_t j = (o + kIndexEdges - 1u) / kIndexEdges; j * kIndexEdges < o + d; ++j) qx[j] = slot;
+// [o, o + d), record the entry's queue slot.  Called by a whole warp, one entry per lane
+// (`valid`); a lane whose entry spans more than 8 boundaries (an R-MAT hub spans
+// hundreds) is helped by the others, so no lane loops alone over a long row.
+__device__ __forceinline__ void index_chunks(uint32_t *qx, uint32_t o, uint32_t d, uint32_t slot, bool valid,
+                                             unsigned lane) {
+  const uint32_t j0 = (o + kIndexEdges - 1u) / kIndexEdges;
+  const uint32_t j1 = valid ? (o + d + kIndexEdges - 1u) / kIndexEdges : j0;
+  const bool big = j1 - j0 > 8u;
+  if (!big)
+    for (uint32_t j = j0; j < j1; ++j) qx[j] = slot;
+  for (unsigned m = __ballot_sync(0xFFFFFFFFu, big); m != 0u; m &= m - 1u) {
+    const int l = __ffs(m) - 1;
+    const uint32_t b0 = __shfl_sync(0xFFFFFFFFu, j0, l), b1 = __shfl_sync(0xFFFFFFFFu, j1, l);
+    const uint32_t bs = __shfl_sync(0xFFFFFFFFu, slot, l);
+    for (uint32_t j = b0 + lane; j < b1; j += 32u) qx[j] = bs;
+  }
 }
 
 struct WarpStage {
@@ -131,7 +152,8 @@ struct WarpStage {
 };
 
 template <int MODE>
-__device__ __forceinline__ void stage_flush(const Params &p, uint32_t out, WarpStage &b, uint32_t n, unsigned lane) {
+__device__ __forceinline__ void stage_flush(const Params &p, uint32_t out, WarpStage &b, uint32_t n, unsigned lane,
+                                            bool index = true) {
   __syncwarp();
   const uint32_t d0 = lane < n ? b.deg[lane] : 0u;
   const uint32_t d1 = lane + 32u < n ? b.deg[lane + 32u] : 0u;
@@ -151,30 +173,31 @@ __device__ __forceinline__ void stage_flush(const Params &p, uint32_t out, WarpS
   if (lane == 0) base = atomicAdd(&p.ctl->qctr[out], ((unsigned long long)n << 32) | (unsigned long long)total);
   base = __shfl_sync(kFull, base, 0);
   const uint32_t bc = (uint32_t)(base >> 32), be = (uint32_t)base;
-  uint32_t *qo = out ? p.qo[1] : p.qo[0];
+  uint32_t *qo = out ? p.qo[1] : p.qo[0];  // the output of an expansion: queue 0 or 1
   uint32_t *qs = out ? p.qs[1] : p.qs[0];
   uint32_t *qv = out ? p.qv[1] : p.qv[0];
   uint32_t *qx = out ? p.qx[1] : p.qx[0];
+  const uint32_t o0 = be + s0 - d0, o1 = be + t0 + s1 - d1;
   if (lane < n) {
-    const uint32_t o = be + s0 - d0;
-    qo[bc + lane] = o;
+    qo[bc + lane] = o0;
     qs[bc + lane] = b.rs[lane];
     if (MODE == MODE_SSSP) qv[bc + lane] = b.v[lane];
-    index_chunks(qx, o, d0, bc + lane);
   }
   if (lane + 32u < n) {
-    const uint32_t o = be + t0 + s1 - d1;
-    qo[bc + 32u + lane] = o;
+    qo[bc + 32u + lane] = o1;
     qs[bc + 32u + lane] = b.rs[lane + 32u];
     if (MODE == MODE_SSSP) qv[bc + 32u + lane] = b.v[lane + 32u];
-    index_chunks(qx, o, d1, bc + 32u + lane);
+  }
+  if (index) {
+    index_chunks(qx, o0, d0, bc + lane, lane < n, lane);
+    if (n > 32u) index_chunks(qx, o1, d1, bc + 32u + lane, lane + 32u < n, lane);
   }
   __syncwarp();
 }
 
 template <int MODE>
 __device__ __forceinline__ void stage_push(const Params &p, uint32_t out, WarpStage &b, uint32_t &n, bool push,
-                                           uint32_t v, uint32_t rs, uint32_t deg, unsigned lane) {
+                                           uint32_t v, uint32_t rs, uint32_t deg, unsigned lane, bool index = true) {
   const unsigned pm = __ballot_sync(kFull, push);
   if (pm == 0u) return;
   if (push) {
@@ -185,7 +208,7 @@ __device__ __forceinline__ void stage_push(const Params &p, uint32_t out, WarpSt
   }
   n += (uint32_t)__popc(pm);
   if (n >= 32u) {
-    stage_flush<MODE>(p, out, b, n, lane);
+    stage_flush<MODE>(p, out, b, n, lane, index);
     n = 0u;
   }
 }
@@ -265,6 +288,8 @@ __host__ __device__ constexpr int traverse_smem(int mode, int nw) {
   return rounded > kTraverseSmemMin ? rounded : kTraverseSmemMin;
 }
 static_assert(traverse_smem(MODE_SSSP, kDefaultWorkerWarps) <= 227 * 1024, "traversal CTA shared memory");
+static_assert(15 * sizeof(Landing<MODE_SSSP>) >= kHistBuckets * sizeof(uint32_t),
+              "an SSSP CTA's landing buffers hold its histogram in a select interval");
 
 __device__ __forceinline__ void cp_async4(void *sdst, const void *gsrc) {
   const uint32_t sa = (uint32_t)__cvta_generic_to_shared(sdst);
@@ -360,6 +385,183 @@ __device__ __forceinline__ void issue_groups(const Params &p, const uint32_t *qo
   cp_async_commit();
 }
 
+// ---- frontier SSSP rounds: select, then expand (Table 1 l-sssp: two barriers per iteration)
+
+// Histogram bucket of tentative distance d in a pending queue whose bucket 0 starts at base.
+__device__ __forceinline__ uint32_t dist_bucket(uint32_t d, uint32_t base) {
+  return d <= base ? 0u : min(kHistBuckets - 1u, (d - base) >> kHistShift);
+}
+
+// Stamp of "queued in the pending queue of round r + 1" during round r (the source is
+// queued for round 0 with stamp 1; a never-queued vertex has stamp 0).
+__device__ __forceinline__ uint32_t sssp_tag(const Interval &iv) { return sssp_round(iv) + 2u; }
+
+// The select interval of round r: split the pending queue (queue iv.sel).  The CTA with
+// logical id `id` owns the queue's 32-entry stripes id * NW + w, id * NW + w + GW, ...
+// (Fig. 4's tid / stride over the current M), spread over the whole queue.  Its first
+// stripe per warp is a sample: a histogram of their out-degrees over their current
+// distances (hs, kHistBuckets words of shared memory) gives the threshold b*, the first
+// bucket at which the sample's cumulative out-degree reaches the fraction of the queue's
+// edges that the round's target B = GW * kNearUnits * kIndexEdges is.  Then the entries
+// in buckets up to b* go to the near queue, any other stays pending for round r + 1 --
+// its stamp advanced so that a lowering in this round's expand interval does not queue it
+// twice -- kSelectBatch stripes per warp at a time, the CTA's warps taking their places
+// in each queue from one atomic of the CTA's (all warps at once on one counter would
+// queue behind each other at the L2).  The least distance
+// selected goes to the control block: the next round's base.  No distance changes in a
+// select interval.  Every selection gives the same result: a vertex whose distance
+// dropped is pending until it has been expanded at that distance, and the traversal ends
+// only when nothing is pending.
+constexpr int kSelectBatch = 4;
+
+template <int NW>
+__device__ __forceinline__ void select_interval(const Params &p, const Interval &iv, int32_t id, uint32_t *hs,
+                                                CtaShared &cs) {
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const unsigned lt = lanemask_lt();
+  const uint32_t in = iv.sel, out = in ^ 1u;
+  const uint32_t GW = (uint32_t)iv.M * NW;
+  const uint32_t F = iv.count, Etot = iv.edges;
+  const uint32_t *qo = queue(p.qo, in), *qs = queue(p.qs, in), *qv = queue(p.qv, in);
+  const uint32_t first = ((uint32_t)id * NW + warp) * 32u;
+  for (uint32_t b = threadIdx.x; b < kHistBuckets; b += NW * 32) hs[b] = 0u;
+  if (threadIdx.x == 0) {
+    cs.split[1] = 0xFFFFFFFFu;
+    cs.take[0][0] = cs.take[0][1] = cs.take[1][0] = cs.take[1][1] = 0ull;
+  }
+  workers_sync<NW>();
+  if (first + lane < F) {
+    const uint32_t i = first + lane;
+    const uint32_t deg = (i + 1u < F ? qo[i + 1u] : Etot) - qo[i];
+    atomicAdd(&hs[dist_bucket((uint32_t)(__ldcg(p.ds + qv[i]) >> 32), iv.base)], deg);
+  }
+  workers_sync<NW>();
+  if (warp == 0) {
+    // the first bucket with cum * Etot >= B * total: lane l sums segment l (32 buckets),
+    // one scan over the segments finds the segment, one more the bucket in it
+    static_assert(kHistBuckets == 32u * 32u, "the threshold search takes 32 segments of 32 buckets");
+    uint32_t seg = 0u;
+#pragma unroll 8
+    for (uint32_t k = 0; k < 32u; ++k) seg += hs[lane * 32u + ((k + lane) & 31u)];  // rotated: no bank conflicts
+    uint32_t sc = seg;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, sc, o);
+      if ((int)lane >= o) sc += y;
+    }
+    const uint64_t want = (uint64_t)GW * kNearUnits * kIndexEdges * __shfl_sync(kFull, sc, 31);
+    const unsigned hs_hit = __ballot_sync(kFull, (uint64_t)sc * Etot >= want);
+    uint32_t bstar = kHistBuckets - 1u;
+    if (hs_hit != 0u) {
+      const uint32_t sg = (uint32_t)(__ffs(hs_hit) - 1);
+      const uint64_t before = __shfl_sync(kFull, sc - seg, (int)sg);  // buckets below segment sg
+      uint32_t b = hs[sg * 32u + lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, b, o);
+        if ((int)lane >= o) b += y;
+      }
+      const unsigned hit = __ballot_sync(kFull, (before + b) * (uint64_t)Etot >= want);
+      bstar = sg * 32u + (uint32_t)(__ffs(hit) - 1);  // the segment's total reaches want: hit != 0
+    }
+    if (lane == 0) cs.split[0] = bstar;
+  }
+  workers_sync<NW>();
+  const uint32_t bstar = cs.split[0];
+  const uint32_t tag = sssp_tag(iv);
+  uint32_t dmin = 0xFFFFFFFFu;
+  const uint32_t step = GW * 32u;
+  // batches: the same count for every warp of the CTA (they meet at two CTA syncs each)
+  const uint32_t nb = (F + kSelectBatch * step - 1u) / (kSelectBatch * step);
+  for (uint32_t bi = 0, i0 = first; bi < nb; ++bi, i0 += kSelectBatch * step) {
+    unsigned long long *take = cs.take[bi & 1u];
+    uint32_t v[kSelectBatch], rs[kSelectBatch], deg[kSelectBatch];
+    bool near[kSelectBatch], far[kSelectBatch];
+#pragma unroll
+    for (int k = 0; k < kSelectBatch; ++k) {
+      const uint32_t i = i0 + (uint32_t)k * step + lane;
+      v[k] = 0u;
+      rs[k] = 0u;
+      deg[k] = 0u;
+      if (i < F) {
+        v[k] = qv[i];
+        rs[k] = qs[i];
+        deg[k] = (i + 1u < F ? qo[i + 1u] : Etot) - qo[i];
+      }
+    }
+    uint32_t nN = 0u, nF = 0u, eN = 0u, eF = 0u;
+#pragma unroll
+    for (int k = 0; k < kSelectBatch; ++k) {
+      const bool valid = i0 + (uint32_t)k * step + lane < F;
+      const uint32_t d = valid ? (uint32_t)(__ldcg(p.ds + v[k]) >> 32) : 0u;
+      near[k] = valid && dist_bucket(d, iv.base) <= bstar;
+      far[k] = valid && !near[k];
+      if (near[k]) dmin = min(dmin, d);
+      nN += (uint32_t)__popc(__ballot_sync(kFull, near[k]));
+      nF += (uint32_t)__popc(__ballot_sync(kFull, far[k]));
+      eN += near[k] ? deg[k] : 0u;
+      eF += far[k] ? deg[k] : 0u;
+    }
+    eN = __reduce_add_sync(kFull, eN);
+    eF = __reduce_add_sync(kFull, eF);
+    // the warp's places within the CTA's part, then the CTA's part of each queue
+    unsigned long long lN = 0ull, lF = 0ull;
+    if (lane == 0) {
+      lN = atomicAdd(&take[0], ((unsigned long long)nN << 32) | eN);
+      lF = atomicAdd(&take[1], ((unsigned long long)nF << 32) | eF);
+    }
+    workers_sync<NW>();
+    if (threadIdx.x == 0) {
+      const unsigned long long tN = take[0], tF = take[1];
+      take[0] = tN ? atomicAdd(&p.ctl->qctr[kNearQueue], tN) : 0ull;
+      take[1] = tF ? atomicAdd(&p.ctl->qctr[out], tF) : 0ull;
+      // every warp read the other parity's bases before the first sync of this batch
+      cs.take[(bi & 1u) ^ 1u][0] = cs.take[(bi & 1u) ^ 1u][1] = 0ull;
+    }
+    workers_sync<NW>();
+    const unsigned long long bN = __shfl_sync(kFull, lN, 0) + take[0];
+    const unsigned long long bF = __shfl_sync(kFull, lF, 0) + take[1];
+    uint32_t atN = (uint32_t)(bN >> 32), oN = (uint32_t)bN, atF = (uint32_t)(bF >> 32), oF = (uint32_t)bF;
+#pragma unroll
+    for (int k = 0; k < kSelectBatch; ++k) {
+      // exclusive scans of this stripe's near and far degrees
+      uint32_t sN = near[k] ? deg[k] : 0u, sF = far[k] ? deg[k] : 0u;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t yN = __shfl_up_sync(kFull, sN, o), yF = __shfl_up_sync(kFull, sF, o);
+        if ((int)lane >= o) {
+          sN += yN;
+          sF += yF;
+        }
+      }
+      const unsigned mN = __ballot_sync(kFull, near[k]), mF = __ballot_sync(kFull, far[k]);
+      const uint32_t atn = atN + (uint32_t)__popc(mN & lt), on = oN + sN - deg[k];
+      const uint32_t atf = atF + (uint32_t)__popc(mF & lt), of = oF + sF - deg[k];
+      if (near[k]) {
+        p.qo[kNearQueue][atn] = on;
+        p.qs[kNearQueue][atn] = rs[k];
+        p.qv[kNearQueue][atn] = v[k];
+      }
+      if (far[k]) {
+        reinterpret_cast<uint32_t *>(p.ds + v[k])[0] = tag;  // the stamp half of the packed word
+        queue(p.qo, out)[atf] = of;
+        queue(p.qs, out)[atf] = rs[k];
+        queue(p.qv, out)[atf] = v[k];
+      }
+      if (mN) index_chunks(p.qx[kNearQueue], on, deg[k], atn, near[k], lane);
+      if (mF) index_chunks(queue(p.qx, out), of, deg[k], atf, far[k], lane);
+      atN += (uint32_t)__popc(mN);
+      atF += (uint32_t)__popc(mF);
+      oN += __shfl_sync(kFull, sN, 31);
+      oF += __shfl_sync(kFull, sF, 31);
+    }
+  }
+  dmin = __reduce_min_sync(kFull, dmin);
+  if (lane == 0 && dmin != 0xFFFFFFFFu) atomicMin(&cs.split[1], dmin);
+  workers_sync<NW>();
+  if (threadIdx.x == 0 && cs.split[1] != 0xFFFFFFFFu) atomicMin(&p.ctl->dmin, cs.split[1]);
+}
+
 // BFS expansion of edges [c0, c1) (the contract is expand_range's).  Software-pipelined
 // like it; per iteration the visited word of every target is read (on small frontiers no
 // pre-check: every target is a candidate) and the targets it shows unvisited are
@@ -450,12 +652,11 @@ __device__ __forceinline__ uint32_t expand_range(const Params &p, const Interval
   const unsigned lane = threadIdx.x & 31u;
   const uint32_t Etot = iv.edges;
   const uint32_t F = iv.count;
-  const uint32_t in = iv.sel, out = in ^ 1u;
-  const uint32_t *qo = in ? p.qo[1] : p.qo[0];
-  const uint32_t *qs = in ? p.qs[1] : p.qs[0];
-  const uint32_t *qv = in ? p.qv[1] : p.qv[0];
+  const uint32_t out = iv.sel ^ 1u;  // the next round's pending queue
+  const uint32_t *qo = queue(p.qo, sssp_xq(iv));  // the near queue, or the whole pending queue
+  const uint32_t *qs = queue(p.qs, sssp_xq(iv));
+  const uint32_t *qv = queue(p.qv, sssp_xq(iv));
   const unsigned lm_le = lanemask_le();
-  const uint32_t next_level = (uint32_t)iv.level + 1u;
   const uint32_t V = (uint32_t)p.V;
   const uint32_t E1 = c1;
   const bool pre = iv.precheck != 0u;
@@ -517,7 +718,7 @@ __device__ __forceinline__ uint32_t expand_range(const Params &p, const Interval
         }
         dv[u] = !val[u] ? 0u : pre ? (uint32_t)(p.ds[vv[u]] >> 32) : 0xFFFFFFFFu;
       }
-      const uint32_t tag = next_level + 1u;  // stamp of "queued for the next round"
+      const uint32_t tag = sssp_tag(iv);  // stamp of "queued for the next round"
       bool imp[kUnroll];
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) {
@@ -610,7 +811,8 @@ __device__ __forceinline__ bool sched_chunk(ChunkSched &sc, uint32_t k, uint32_t
 
 // Expand this warp's part of the interval, chunk by chunk (ChunkSched).  The enqueue
 // built a chunk index (the entry holding every kIndexEdges-th edge), so a chunk starts
-// without any search.
+// without any search.  BFS expands queue iv.sel into the other one; SSSP queue xq (the
+// near queue, or a small pending queue whole) into the next pending queue.
 template <int MODE, int NW>
 __device__ void expand(const Params &p, const Interval &iv, int32_t id, WarpStage &stage, Landing<MODE> &pf) {
   const unsigned lane = threadIdx.x & 31u;
@@ -620,7 +822,7 @@ __device__ void expand(const Params &p, const Interval &iv, int32_t id, WarpStag
   sched_init(sc, Etot, GW, MODE == MODE_SSSP ? kChunkUnitsMaxSssp : kChunkUnitsMax);
   uint32_t c0 = 0u, c1 = 0u;
   if (!sched_chunk(sc, (uint32_t)id * NW + (threadIdx.x >> 5), Etot, GW, c0, c1)) return;
-  const uint32_t *qx = iv.sel ? p.qx[1] : p.qx[0];
+  const uint32_t *qx = MODE == MODE_SSSP ? queue(p.qx, sssp_xq(iv)) : iv.sel ? p.qx[1] : p.qx[0];
   const uint32_t out = iv.sel ^ 1u;
   uint32_t staged = 0u, nreach = 0u;
   uint32_t ch = 0u, ct = 0u;  // BFS claim ring: head and tail (warp-uniform)
@@ -890,8 +1092,16 @@ __device__ __forceinline__ void worker_loop(const Params &p, CtaShared &cs, Warp
       return;
     }
     if (id >= iv.M) return;  // left through offer_kill
-    if constexpr (MODE == MODE_PSSSP) topo_interval<NW>(p, iv, id);
-    else if constexpr (MODE != MODE_BARRIER) expand<MODE, NW>(p, iv, id, stage, pf);
+    if constexpr (MODE == MODE_PSSSP) {
+      topo_interval<NW>(p, iv, id);
+    } else if constexpr (MODE == MODE_SSSP) {
+      // the landing buffers are idle in a select interval: their first kHistBuckets words
+      // hold the CTA's histogram
+      if (sssp_select(iv)) select_interval<NW>(p, iv, id, reinterpret_cast<uint32_t *>(pfs), cs);
+      else expand<MODE, NW>(p, iv, id, stage, pf);
+    } else if constexpr (MODE != MODE_BARRIER) {
+      expand<MODE, NW>(p, iv, id, stage, pf);
+    }
     if (!resizing_barrier<MODE, NW>(p, cs)) return;
   }
 }
@@ -1594,8 +1804,9 @@ struct coop_ctx {
   int64_t cap_V = 0, cap_chunks = 0;
   uint32_t *visited = nullptr;
   unsigned long long *ds = nullptr;
-  uint32_t *qx[2] = {nullptr, nullptr};
-  uint32_t *qv[2] = {nullptr, nullptr}, *qs[2] = {nullptr, nullptr}, *qo[2] = {nullptr, nullptr};
+  uint32_t *qx[3] = {nullptr, nullptr, nullptr};
+  uint32_t *qv[3] = {nullptr, nullptr, nullptr}, *qs[3] = {nullptr, nullptr, nullptr};
+  uint32_t *qo[3] = {nullptr, nullptr, nullptr};
   std::mutex mu;         // host bookkeeping (kill/fork counters, run state)
   std::mutex launch_mu;  // serialises traversal launches
   uint32_t run = 0;
@@ -1718,7 +1929,7 @@ coop_status ensure_scratch(coop_ctx *c, int64_t V, int64_t E) {
   const size_t words = (size_t)(cap + 31) / 32;
   const size_t qbytes = (size_t)cap * 4;
   const size_t xbytes = (size_t)capx * 4;
-  const size_t total = words * 4 + qbytes * 8 + xbytes * 2 + 10 * 256;
+  const size_t total = words * 4 + qbytes * 11 + xbytes * 3 + 14 * 256;
   char *base = nullptr;
   if (cudaMalloc(&base, total) != cudaSuccess) {
     (void)cudaGetLastError();
@@ -1731,7 +1942,7 @@ coop_status ensure_scratch(coop_ctx *c, int64_t V, int64_t E) {
     return reinterpret_cast<uint32_t *>(p);
   };
   c->visited = take(words * 4);
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < 3; ++i) {
     c->qv[i] = take(qbytes);
     c->qs[i] = take(qbytes);
     c->qo[i] = take(qbytes);
@@ -1803,7 +2014,7 @@ coop_status launch_run(coop_ctx *c, const coop_csr *g, const uint32_t *w, int32_
     p.dist = dist;
     p.visited = c->visited;
     p.ds = c->ds;
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 3; ++i) {
       p.qv[i] = c->qv[i];
       p.qs[i] = c->qs[i];
       p.qo[i] = c->qo[i];
@@ -2323,14 +2534,14 @@ coop_status coop_batch_create(coop_ctx *c, const coop_job *jobs, int n, coop_bat
   b->ctx = c;
   b->n = n;
   b->jobs.assign(jobs, jobs + n);
-  // scratch per job: control block, mailbox, bitmap or stamps, 2 x 3 queues, 2 chunk indexes
+  // scratch per job: control block, mailbox, bitmap or stamps, 3 x 3 queues, 3 chunk indexes
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   std::vector<size_t> off(n + 1, 0);
   for (int i = 0; i < n; ++i) {
     const size_t V = (size_t)jobs[i].graph.num_vertices, X = (size_t)(jobs[i].graph.num_edges / kIndexEdges + 2);
     const size_t need = al(sizeof(Ctl)) + al(sizeof(Mailbox)) +
-                        (jobs[i].kind == COOP_JOB_SSSP ? al(V * 8) : al((V + 31) / 32 * 4)) + 6 * al(V * 4) +
-                        2 * al(X * 4);
+                        (jobs[i].kind == COOP_JOB_SSSP ? al(V * 8) : al((V + 31) / 32 * 4)) + 9 * al(V * 4) +
+                        3 * al(X * 4);
     off[i + 1] = off[i] + need;
     b->max_V = std::max<int64_t>(b->max_V, (int64_t)V);
   }
@@ -2361,12 +2572,12 @@ coop_status coop_batch_create(coop_ctx *c, const coop_job *jobs, int n, coop_bat
     p.mbox = reinterpret_cast<Mailbox *>(take(sizeof(Mailbox)));
     if (j.kind == COOP_JOB_SSSP) p.ds = reinterpret_cast<unsigned long long *>(take(V * 8));
     else p.visited = reinterpret_cast<uint32_t *>(take((V + 31) / 32 * 4));
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < 3; ++q) {
       p.qv[q] = reinterpret_cast<uint32_t *>(take(V * 4));
       p.qs[q] = reinterpret_cast<uint32_t *>(take(V * 4));
       p.qo[q] = reinterpret_cast<uint32_t *>(take(V * 4));
     }
-    for (int q = 0; q < 2; ++q) p.qx[q] = reinterpret_cast<uint32_t *>(take(X * 4));
+    for (int q = 0; q < 3; ++q) p.qx[q] = reinterpret_cast<uint32_t *>(take(X * 4));
     p.row_off = j.graph.row_off;
     p.col = j.graph.col;
     p.V = j.graph.num_vertices;

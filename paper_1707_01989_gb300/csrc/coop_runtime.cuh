@@ -68,6 +68,22 @@ constexpr uint32_t kPrecheckEdges = 65536;
 // (An R-MAT hub's 10^4-10^5 edges on one warp would leave the rest of the grid waiting.)
 constexpr uint32_t kTopoHeavy = 512;
 constexpr uint32_t kTopoChunk = 256;
+// Frontier SSSP in rounds (Table 1 l-sssp: two barriers per iteration).  A round whose
+// pending queue has more than kNearUnits * kIndexEdges out-edges per worker warp has two
+// intervals: a select interval moves the pending vertices of lowest tentative distance,
+// about that many out-edges, into the near queue (queue kNearQueue) and defers the rest
+// to the next round's pending queue; the expand interval relaxes the near queue's
+// out-edges into that pending queue.  A smaller pending queue is expanded whole, in one
+// interval.  Each CTA splits its own stripes of the pending queue at a distance threshold
+// found from a sample of its stripes: a histogram of their out-degrees over current
+// distance in kHistBuckets buckets of 2^kHistShift distance units above the round's
+// base (no pending distance is below it; the last bucket takes every larger distance).
+// Relaxing the closest vertices first keeps most vertices from being expanded again at a
+// distance that later drops (work inflation).
+constexpr uint32_t kNearQueue = 2;
+constexpr uint32_t kNearUnits = 4;
+constexpr uint32_t kHistBuckets = 1024;
+constexpr uint32_t kHistShift = 2;
 
 // MODE_PSSSP: topology-driven SSSP (Table 1's p-sssp, read as Pannotia's formulation):
 // every iteration scans all vertices in three intervals -- relax, update, check.
@@ -92,7 +108,7 @@ enum Err : int {
 // out_nodes) plus the active count M that holds during the interval.
 struct Interval {
   int32_t M;       // active CTAs in this interval
-  int32_t level;   // BFS level / SSSP round whose frontier is expanded
+  int32_t level;   // BFS level whose frontier is expanded / SSSP interval (round = level / 2)
   uint32_t sel;    // input queue index; the output queue is sel ^ 1
   uint32_t count;  // frontier vertices in the input queue
   uint32_t edges;  // frontier out-edges (size of this interval's edge space)
@@ -100,7 +116,19 @@ struct Interval {
   uint32_t epoch;  // epoch number that opened this interval
   uint32_t doom;   // CTAs of the previous interval with logical id >= doom leave (host kills)
   uint32_t precheck;  // 1: read a target's state before its claim atomic (kPrecheckEdges)
+  uint32_t base;      // SSSP: the round's histogram base (no pending distance is below it)
+  // SSSP: round r << 3 | select << 2 | xq.  Round r's pending queue is queue sel, the
+  // next round's sel ^ 1; select is 1 in a round's select interval, 0 in an expand
+  // interval, which expands queue xq (kNearQueue, or the pending queue whole)
+  uint32_t sssp;
 };
+
+__host__ __device__ constexpr uint32_t sssp_word(uint32_t round, uint32_t select, uint32_t xq) {
+  return round << 3 | select << 2 | xq;
+}
+__host__ __device__ constexpr uint32_t sssp_round(const Interval &iv) { return iv.sssp >> 3; }
+__host__ __device__ constexpr bool sssp_select(const Interval &iv) { return ((iv.sssp >> 2) & 1u) != 0u; }
+__host__ __device__ constexpr uint32_t sssp_xq(const Interval &iv) { return iv.sssp & 3u; }
 
 // One barrier record (the run's trace): barrier index, microseconds since the run
 // started, the active count before, CTAs admitted (fork), CTAs leaving (kill), the active
@@ -121,8 +149,8 @@ struct Ctl {
   Word epoch;         // release word: bumped by the releaser
   Word join_ticket;   // registrations of CTAs waiting to be admitted
   Word cursor;        // chunks claimed beyond the first M * NW in the current interval
-  alignas(128) unsigned long long qctr[2];  // per queue: (vertices << 32) | edges
-  uint64_t pad_q[14];
+  alignas(128) unsigned long long qctr[3];  // per queue: (vertices << 32) | edges
+  uint64_t pad_q[13];
   alignas(128) Interval iv;  // the current interval (written only by releasers)
   uint32_t pad_iv[24];
   // host kill target of the running interval: (epoch << 32) | closed << 31 | T, where
@@ -155,6 +183,10 @@ struct Ctl {
   unsigned long long t_start;  // %globaltimer at the master's entry
   uint32_t log_n;
   uint32_t pad_b[13];
+  // SSSP: least distance selected in the current round (atomicMin by the select's CTAs),
+  // the next round's histogram base
+  alignas(128) uint32_t dmin;
+  uint32_t pad_s[31];
   alignas(128) unsigned long long slot[kMaxCtas];  // admission records, by ticket % kMaxCtas
   LogRec log[kLogCap];
 };
@@ -188,10 +220,11 @@ struct Params {
   // round the vertex was last queued for; the distances are copied out to `dist` when
   // the traversal ends
   unsigned long long *ds;
-  uint32_t *qv[2];    // frontier queues: vertex id (SSSP)
-  uint32_t *qs[2];    //                  first column index (row_off[v])
-  uint32_t *qo[2];    //                  exclusive prefix of out-degrees (edge space)
-  uint32_t *qx[2];    // chunk index: entry holding edge j * kIndexEdges, per queue
+  // frontier queues 0 and 1 (BFS levels, SSSP pending vertices) and 2 (SSSP near queue)
+  uint32_t *qv[3];    // vertex id (SSSP)
+  uint32_t *qs[3];    // first column index (row_off[v])
+  uint32_t *qo[3];    // exclusive prefix of out-degrees (edge space)
+  uint32_t *qx[3];    // chunk index: entry holding edge j * kIndexEdges, per expanded queue
   Ctl *ctl;
   Mailbox *mbox;
   int32_t V;
@@ -220,6 +253,10 @@ struct Params {
 
 struct CtaShared {
   Interval iv;
+  uint32_t split[2];  // SSSP select interval: threshold bucket, least distance selected
+  // SSSP select interval, by batch parity: per queue (near, pending) the CTA's
+  // (entries << 32 | edges) of a batch, then the CTA's base in the queue
+  unsigned long long take[2][2];
   int32_t id;
   int32_t ok;
   int32_t exit;
@@ -335,7 +372,8 @@ __device__ __forceinline__ void raise_err(const Params &p, int code) {
 __device__ __forceinline__ void publish_stats(const Params &p, int status) {
   Ctl *c = p.ctl;
   Mailbox *m = p.mbox;
-  st_sys((uint32_t *)&m->levels, (uint32_t)c->iv.level);
+  // SSSP: rounds (an expand interval each, some also a select interval)
+  st_sys((uint32_t *)&m->levels, p.mode == MODE_SSSP ? sssp_round(c->iv) : (uint32_t)c->iv.level);
   st_sys((uint32_t *)&m->barriers, (uint32_t)c->barriers);
   st_sys((uint32_t *)&m->kills, (uint32_t)c->kills);
   st_sys((uint32_t *)&m->forks, (uint32_t)c->forks);
@@ -443,7 +481,13 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
   const uint32_t out = cur.sel ^ 1u;
   // the output queue's (vertices << 32 | edges); topology-driven SSSP: the vertices its
   // update interval lowered, and the edges its relax interval scanned
-  const unsigned long long packed = (MODE == MODE_BARRIER) ? 0ull : (MODE == MODE_PSSSP) ? c->qctr[0] : c->qctr[out];
+  // SSSP: after a select the near queue is expanded next, after an expand the pending queue
+  const bool was_select = MODE == MODE_SSSP && sssp_select(cur);
+  const unsigned long long packed = (MODE == MODE_BARRIER) ? 0ull
+                                    : (MODE == MODE_PSSSP) ? c->qctr[0]
+                                    : was_select           ? c->qctr[kNearQueue]
+                                                           : c->qctr[out];
+  const uint32_t dmin = (MODE == MODE_SSSP && !was_select) ? ld_relaxed(&c->dmin) : 0xFFFFFFFFu;
   const unsigned long long relaxed = (MODE == MODE_PSSSP) ? c->qctr[1] : 0ull;
   const uint32_t A = c->admitted;
   const uint32_t decided = c->host_decided;
@@ -481,6 +525,23 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
     }
     // the relax interval has used the heavy-row list: the next update builds it anew
     if ((uint32_t)cur.level % 3u == 0u) c->cursor.v = 0u;
+  } else if (MODE == MODE_SSSP) {
+    count = (uint32_t)(packed >> 32);
+    edges = (uint32_t)packed;
+    c->cursor.v = 0u;
+    c->qctr[cur.sel] = 0ull;  // this round's pending queue is used up: it holds round r + 2's
+    if (was_select) {
+      nxt.sssp = sssp_word(sssp_round(cur), 0u, kNearQueue);
+    } else {
+      c->qctr[kNearQueue] = 0ull;
+      nxt.sel = out;
+      // every distance of round r + 1 is above the least one expanded in round r (recorded
+      // by a select interval; without one the old base still bounds it)
+      if (dmin != 0xFFFFFFFFu) nxt.base = dmin;
+      st_relaxed(&c->dmin, 0xFFFFFFFFu);
+      const uint64_t B = (uint64_t)M * NW * kNearUnits * kIndexEdges;
+      nxt.sssp = sssp_word(sssp_round(cur) + 1u, (uint64_t)edges > B ? 1u : 0u, out);
+    }
   } else {
     count = (uint32_t)(packed >> 32);
     edges = (uint32_t)packed;
@@ -490,7 +551,9 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
   }
   nxt.count = count;
   nxt.edges = edges;
-  nxt.done = (count == 0u || err != 0u) ? 1u : 0u;
+  // an SSSP round's expand interval runs even on an empty near queue: the traversal ends
+  // when a round leaves nothing pending
+  nxt.done = ((count == 0u && !was_select) || err != 0u) ? 1u : 0u;
 
   const int32_t Wmid = M - Mmid;
   int32_t k = 0, W = 0, spawned = 0;
@@ -537,8 +600,11 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
   bk.forks = forks0 + k;
   bk.min_active = min(mina, min(Mmid, Mn));
   bk.max_active = max(maxa, Mn);
-  bk.edges_scanned = nxt.done ? es0 : es0 + edges;
-  bk.frontier_total = nxt.done ? ft0 : ft0 + count;
+  // edges and vertices of the frontiers the traversal expands (SSSP: not the pending
+  // queues that a select interval splits)
+  const bool expands = !nxt.done && (MODE != MODE_SSSP || !sssp_select(nxt));
+  bk.edges_scanned = expands ? es0 + edges : es0;
+  bk.frontier_total = expands ? ft0 + count : ft0;
   // every barrier while the first half of the trace has room, resize events always
   const int32_t t_us = (int32_t)((now - t_start) / 1000ull);
   bk.has_kill = Wmid > 0 && log_n < (uint32_t)kLogCap;  // the host kills of the interval
@@ -734,6 +800,9 @@ __device__ __forceinline__ void master_enter(const Params &p, CtaShared &cs) {
   iv.epoch = 1u;
   iv.doom = (uint32_t)(1 + k);
   iv.precheck = precheck_hint(edges);
+  iv.base = 0u;
+  iv.sssp = sssp_word(0u, 0u, 0u);  // SSSP round 0 expands the source's pending queue whole
+  c->dmin = 0xFFFFFFFFu;
   c->admitted = (uint32_t)k;
   c->live = (unsigned long long)(uint32_t)iv.M << 32;
   c->t_start = gtime();
