@@ -304,6 +304,7 @@ def measure(coop, ctx, dev, stream, flush, name, steps, warmup, world=1, cpu_bud
         "stats": {"levels": st.levels, "barriers": st.barriers, "frontier_total": st.frontier_total,
                   "edges_expanded": st.edges_scanned, "work_inflation": round(st.edges_scanned / max(es, 1), 3)},
     }
+    ref = None
     if cpu_budget is not None:
         ref, times = time_cpu_oracle(g, w, src, trav, budget_s=cpu_budget)
         res["parity_last_step"] = bool(np.array_equal(ref, last)) and bool(np.array_equal(ref, e2e_out))
@@ -312,7 +313,7 @@ def measure(coop, ctx, dev, stream, flush, name, steps, warmup, world=1, cpu_bud
             "value": round(es / statistics.mean(times) / 1e9, 6), "unit": "GTEPS", "cores": 1, "kind": "oracle",
             "sample": f"{len(times)} full {algo} traversal(s) of the {name} workload on 1 host core "
                       f"({os.cpu_count()} cores present)"}
-    res["_graph"] = (g, src, ro, col, csr)  # reused by the secondary figures on the same graph
+    res["_graph"] = (g, src, ro, col, csr, ref)  # reused by the secondary figures on the same graph
     return res
 
 
@@ -495,6 +496,7 @@ def corunner(coop, ctx, dev, csr, src, lv, stream, period_s=1.0 / 60.0, duration
             time.sleep(max(0.0, nxt - time.perf_counter()))
 
     th = threading.Thread(target=ticker)
+    coop.coop_get_request_log(ctx, clear=True)
     t0 = time.perf_counter()
     th.start()
     n_co = 0
@@ -506,6 +508,8 @@ def corunner(coop, ctx, dev, csr, src, lv, stream, period_s=1.0 / 60.0, duration
     stop.set()
     th.join()
     coop.coop_sync(ctx)
+    reqs = coop.coop_get_request_log(ctx, clear=True)
+    slowest = sorted(reqs, key=lambda r: -r["gather_us"])[:3]
 
     def pct(v, q):
         v = sorted(v)
@@ -519,6 +523,8 @@ def corunner(coop, ctx, dev, csr, src, lv, stream, period_s=1.0 / 60.0, duration
             "deadline_ms": 2.0, "deadline_met_frac": round(sum(l <= 2.0 for l in lat) / max(1, len(lat)), 4),
             "traversal_ms_alone": round(per_alone * 1e3, 4), "traversal_ms_corun": round(per_co * 1e3, 4),
             "coop_slowdown": round(per_co / per_alone, 4),
+            # per-request records of the three slowest gathers: M when posted and granted
+            "slowest_gathers": [{k: round(v, 1) for k, v in r.items()} for r in slowest],
             **({} if work is None else {
                 # host-timed back-to-back traversals (launch gaps included)
                 "gteps_alone": round(work[0] / per_alone / 1e9, 3), "gteps_corun": round(work[0] / per_co / 1e9, 3),
@@ -610,6 +616,190 @@ def preemption(coop, ctx, dev, stream, period_s=1.0 / 60.0, duration_s=1.0):
             "coop": {"jobs": len(lat_coop), "latency_ms_p50": pct(lat_coop, 0.5),
                      "latency_ms_p99": pct(lat_coop, 0.99), "traversal_ms": round(per_coop * 1e3, 4)},
             "p99_no_coop_vs_coop": round(pct(lat_plain, 0.99) / pct(lat_coop, 0.99), 3)}
+
+
+# The graphics workload classes of Sec. 5.5's Table 3: period P, duration E (ms) and the
+# share of the CTAs the non-cooperative task claims.
+TABLE3_CLASSES = (("light", 70.0, 3.0, 4), ("medium", 40.0, 3.0, 4), ("heavy", 40.0, 10.0, 2))
+
+
+def table3(coop, ctx, dev, stream, csr, src, lv, ref, duration_s=1.0, classes=TABLE3_CLASSES):
+    """Sec. 5.5 / Table 3: the cooperative kernel's slowdown under periodic
+    non-cooperative work, against kernel-level preemption.
+
+    For each class (P, E, N/d) the non-cooperative task is a job of back-to-back saxpy
+    launches on N/d CTAs sized to run E ms alone (its measured duration is D).  The
+    cooperative kernel is back-to-back R-MAT 22 BFS traversals for `duration_s`; every P
+    ms the task asks for N/d CTAs, runs, and gives them back.  Cooperative slowdown =
+    traversal time with the task / without.  Non-cooperative: the baseline kernel
+    (fixed CTAs, no scheduler) with the job on a high-priority stream -- its CTAs wait
+    for a traversal to end and the next traversal cannot pass its first barrier until the
+    job is done, so the compute kernel is effectively preempted for D every P; the model
+    of the paper for that is P / (P - D).  Each run's last levels are checked against the
+    oracle."""
+    import numpy as np
+    import torch
+    N = coop.coop_query(ctx)["max_ctas"]
+    n_el = 16 * 1024 * 1024
+    x = torch.rand(n_el, device=dev)
+    y = torch.rand(n_el, device=dev)
+    cs = torch.cuda.Stream(device=dev, priority=-1)
+    trav_coop = lambda: coop.coop_bfs(ctx, csr, src, lv, stream=stream)
+    trav_plain = lambda: coop.coop_bfs_baseline(ctx, csr, src, lv, stream=stream)
+
+    def job_alone(k, reps):
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            coop.coop_saxpy(k, 2.0, x, y, stream=cs)
+        cs.synchronize()
+        return (time.perf_counter() - t0) * 1e3
+
+    def rate(traverse, secs):
+        traverse()
+        stream.synchronize()
+        t0 = time.perf_counter()
+        n = 0
+        while time.perf_counter() - t0 < secs:
+            traverse()
+            n += 1
+        stream.synchronize()
+        return (time.perf_counter() - t0) / n
+
+    def corun(traverse, job, period_ms):
+        lat, starts = [], []
+        stop = threading.Event()
+
+        def ticker():
+            nxt = time.perf_counter()
+            while not stop.is_set():
+                starts.append(time.perf_counter())
+                lat.append(job())
+                nxt += period_ms / 1e3
+                time.sleep(max(0.0, nxt - time.perf_counter()))
+
+        traverse()
+        stream.synchronize()
+        th = threading.Thread(target=ticker)
+        t0 = time.perf_counter()
+        th.start()
+        n = 0
+        while time.perf_counter() - t0 < duration_s:
+            traverse()
+            n += 1
+        stream.synchronize()
+        per = (time.perf_counter() - t0) / n
+        stop.set()
+        th.join()
+        exact = bool(np.array_equal(lv.cpu().numpy(), ref))
+        gaps = np.diff(starts) * 1e3 if len(starts) > 1 else np.array([0.0])
+        return per, lat, float(np.median(gaps)), exact
+
+    def pct(v, q):
+        v = sorted(v)
+        return round(v[min(len(v) - 1, int(round(q * (len(v) - 1))))], 3)
+
+    alone_coop = rate(trav_coop, 0.4)
+    alone_plain = rate(trav_plain, 0.4)
+    coop.coop_sync(ctx)
+    rows = []
+    for name, P, E, d in classes:
+        k = N // d
+        one = statistics.median(job_alone(k, 1) for _ in range(5))
+        reps = max(1, int(round(E / max(one, 1e-3))))
+        D = statistics.median(job_alone(k, reps) for _ in range(5))
+
+        def coop_job():
+            t0 = time.perf_counter()
+            got = coop.coop_request_resources(ctx, k, timeout_us=2_000_000)
+            for _ in range(reps):
+                coop.coop_saxpy(k, 2.0, x, y, stream=cs)
+            cs.synchronize()
+            t1 = time.perf_counter()
+            coop.coop_release(ctx, got)
+            return (t1 - t0) * 1e3
+
+        def plain_job():
+            return job_alone(k, reps)
+
+        per_c, lat_c, per_task_c, ok_c = corun(trav_coop, coop_job, P)
+        coop.coop_sync(ctx)
+        per_p, lat_p, per_task_p, ok_p = corun(trav_plain, plain_job, P)
+        rows.append({
+            "class": name, "period_ms": P, "task_ms": round(D, 3), "task_ctas": k, "task_launches": reps,
+            "model_P_over_P_minus_D": round(P / (P - D), 3),
+            "coop_slowdown": round(per_c / alone_coop, 3), "no_coop_slowdown": round(per_p / alone_plain, 3),
+            "coop_task_latency_ms_p50": pct(lat_c, 0.5), "coop_task_latency_ms_p99": pct(lat_c, 0.99),
+            "no_coop_task_latency_ms_p99": pct(lat_p, 0.99),
+            "coop_task_period_ms": round(per_task_c, 2), "no_coop_task_period_ms": round(per_task_p, 2),
+            "coop_deadline_met_frac": round(sum(l <= P for l in lat_c) / max(1, len(lat_c)), 3),
+            "tasks": len(lat_c), "bit_exact": ok_c and ok_p})
+    return {"graph": "R-MAT 22 BFS, back to back", "traversal_ms_alone": round(alone_coop * 1e3, 4),
+            "baseline_traversal_ms_alone": round(alone_plain * 1e3, 4), "classes": rows}
+
+
+def occupancy_trace(coop, ctx, dev, stream, period_s=0.0005, runs=40):
+    """SM occupancy over time: active CTAs M at every resizing barrier of one traversal
+    while a co-runner takes half the CTAs (saxpy over 64 MB) every `period_s` and gives
+    them back -- the kernel shrinking to N/2 and growing back.  Grid 256x256 BFS (511
+    barriers, about 6 us apart) and R-MAT 22 BFS (6 barriers).  Returns, per graph, the
+    traversal among `runs` back-to-back ones with the most resize events: its trace
+    as (t_us, M_after) at the barriers where M changed, and the number of barriers spent
+    at each M."""
+    import numpy as np
+    import torch
+    import graphgen as gg
+    N = coop.coop_query(ctx)["max_ctas"]
+    half = N // 2
+    x = torch.rand(16 << 20, device=dev)
+    y = torch.rand(16 << 20, device=dev)
+    cs = torch.cuda.Stream(device=dev, priority=-1)
+    out = {}
+    for name, g, src in (("grid256_bfs", gg.grid(256, 256), 0), ("rmat22_bfs", gg.rmat(22, 16, seed=22), None)):
+        src = gg.max_out_degree_vertex(g) if src is None else src
+        ro = torch.from_numpy(np.array(g.row_off)).to(dev)
+        col = torch.from_numpy(np.array(g.col)).to(dev)
+        lv = torch.empty(g.num_vertices, dtype=torch.int32, device=dev)
+        csr = coop.make_csr(ro, col)
+        stop = threading.Event()
+
+        def ticker():
+            nxt = time.perf_counter()
+            while not stop.is_set():
+                got = coop.coop_request_resources(ctx, half, timeout_us=2_000_000)
+                coop.coop_saxpy(half, 2.0, x, y, stream=cs)
+                cs.synchronize()
+                coop.coop_release(ctx, got)
+                nxt += period_s
+                time.sleep(max(0.0, nxt - time.perf_counter()))
+
+        th = threading.Thread(target=ticker)
+        th.start()
+        best = None
+        try:
+            for _ in range(runs):
+                st = coop.coop_bfs(ctx, csr, src, lv, stream=stream, stats=True)
+                log = coop.coop_get_resize_log(ctx)
+                events = sum(1 for r in log if r[3] or r[4])
+                if best is None or events > best[0]:
+                    best = (events, log, st)
+        finally:
+            stop.set()
+            th.join()
+        coop.coop_sync(ctx)
+        _, log, st = best
+        trace, m = [], None
+        for r in log:  # (barrier, t_us, M_before, k, W, M_after, spawned, edges)
+            if m is None or r[5] != m:
+                trace.append((r[1], r[5]))
+                m = r[5]
+        dwell = {}
+        for r in log:
+            dwell[r[5]] = dwell.get(r[5], 0) + 1
+        out[name] = {"N": N, "barriers": st.barriers, "kills": st.kills, "forks": st.forks,
+                     "min_active": st.min_active, "kernel_us": round(st.kernel_us, 1),
+                     "trace_t_us_M": trace[:200], "barriers_at_M": dict(sorted(dwell.items()))}
+        del ro, col, lv
+    return out
 
 
 def gather_by_kill_mode(coop, ctx, dev, stream, period_s=0.005, duration_s=0.6):
@@ -965,8 +1155,8 @@ def serving(coop, dev, n_graphs=32, rate=200.0, duration_s=3.0, slots=4, budget=
             "all_ok": all(r.status == 0 for r in done)}
 
 
-EXTRAS = ("sssp_rmat20", "bfs_rmat22", "grid_bfs", "preemption", "gather_by_kill_mode", "topology_driven_sssp",
-          "octree", "batched", "serving", "barrier_us")
+EXTRAS = ("sssp_rmat20", "bfs_rmat22", "grid_bfs", "preemption", "gather_by_kill_mode", "occupancy_trace",
+          "topology_driven_sssp", "octree", "batched", "serving", "barrier_us")
 
 
 def selected_extras(spec: str):
@@ -1036,20 +1226,24 @@ def secondary(coop, ctx, dev, stream, flush, args, head):
 
     def rmat22():
         # BFS on R-MAT scale 22: the non-cooperative baseline, schedules and the co-runner
+        ref = None
         if args.workload == "rmat22-bfs":
-            g, src, ro, col, csr = head["_graph"]
+            g, src, ro, col, csr, ref = head["_graph"]
         else:
             g = gg.rmat(22, 16, seed=22)
             src = gg.max_out_degree_vertex(g)
             ro = torch.from_numpy(np.array(g.row_off)).to(dev)
             col = torch.from_numpy(np.array(g.col)).to(dev)
             csr = coop.make_csr(ro, col)
+        if ref is None:
+            ref = oracle_run(g, None, src, "bfs")
         lv = torch.empty(g.num_vertices, dtype=torch.int32, device=dev)
         f = lambda: coop.coop_bfs(ctx, csr, src, lv, stream=stream)
         for _ in range(3):
             f()
         ms, kus = timed(f, max(3, args.steps))
         lvh = lv.cpu().numpy()
+        assert np.array_equal(lvh, ref), "R-MAT 22 BFS levels differ from the oracle"
         vr, es = reached_work(g, lvh >= 0)
         B = 4 * g.num_vertices + 20 * vr + 8 * es
         fb = lambda: coop.coop_bfs_baseline(ctx, csr, src, lv, stream=stream)
@@ -1062,6 +1256,7 @@ def secondary(coop, ctx, dev, stream, flush, args, head):
                               "baseline_kernel_us": round(kusb, 2), "coop_overhead": round(kus / kusb, 4)}}
         res["bfs_rmat22_schedules"] = random_schedules(coop, ctx, csr, src, lv, lvh, stream, es)
         res["corunner"] = corunner(coop, ctx, dev, csr, src, lv, stream, work=(es, B, hbm))
+        res["table3"] = table3(coop, ctx, dev, stream, csr, src, lv, lvh)
         return res
 
     def grid():
@@ -1109,6 +1304,7 @@ def secondary(coop, ctx, dev, stream, flush, args, head):
         "grid_bfs": lambda: guarded("grid_bfs", grid),
         "preemption": lambda: guarded("preemption", lambda: preemption(coop, ctx, dev, stream)),
         "gather_by_kill_mode": lambda: guarded("gather_by_kill_mode", lambda: gather_by_kill_mode(coop, ctx, dev, stream)),
+        "occupancy_trace": lambda: guarded("occupancy_trace", lambda: occupancy_trace(coop, ctx, dev, stream)),
         "topology_driven_sssp": lambda: guarded("topology_driven_sssp",
                                                 lambda: topology_driven(coop, ctx, dev, stream, flush)),
         "octree": lambda: guarded("octree", lambda: octree(coop, ctx, dev, stream, flush)),

@@ -21,6 +21,7 @@ __all__ = [
     "CoopError", "CoopUnavailable", "Stats", "CSR", "coop_init", "coop_destroy", "coop_bfs", "coop_sssp",
     "coop_sssp_topo", "coop_octree",
     "coop_request_resources", "coop_release", "coop_sync", "coop_get_stats", "coop_get_resize_log",
+    "coop_get_request_log", "REQUEST_FIELDS",
     "coop_set_schedule", "coop_set_timeout", "coop_set_timing", "coop_set_kill_mode", "COOP_KILL_CHUNK",
     "COOP_KILL_QUERY", "COOP_KILL_SIMPLE", "coop_query", "coop_bfs_baseline", "coop_sssp_baseline",
     "coop_barrier_bench", "coop_saxpy", "coop_bfs_noalloc", "coop_status_string", "Job", "Batch", "make_job",
@@ -119,6 +120,7 @@ def load_library():
                 "coop_sync": [vp],
                 "coop_get_stats": [vp, sp],
                 "coop_get_resize_log": [vp, ctypes.POINTER(i32), ctypes.c_int, ip],
+                "coop_get_request_log": [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ip, ctypes.c_int],
                 "coop_set_schedule": [vp, u64, ctypes.c_double, ctypes.c_double],
                 "coop_set_timeout": [vp, i64],
                 "coop_set_timing": [vp, ctypes.c_int],
@@ -349,6 +351,18 @@ def coop_get_resize_log(ctx, cap: int = 4096):
     n = ctypes.c_int(0)
     _check(load_library().coop_get_resize_log(_h(ctx), buf, cap, ctypes.byref(n)), "coop_get_resize_log")
     return [tuple(buf[8 * i: 8 * i + 8]) for i in range(n.value)]
+
+
+REQUEST_FIELDS = ("t_us", "n_ctas", "active_at_post", "active_at_grant", "gather_us", "granted")
+
+
+def coop_get_request_log(ctx, cap: int = 4096, clear: bool = True):
+    """The context's coop_request_resources records, oldest first, as dicts of REQUEST_FIELDS."""
+    buf = (ctypes.c_double * (6 * cap))()
+    n = ctypes.c_int(0)
+    _check(load_library().coop_get_request_log(_h(ctx), buf, cap, ctypes.byref(n), 1 if clear else 0),
+           "coop_get_request_log")
+    return [dict(zip(REQUEST_FIELDS, buf[6 * i: 6 * i + 6])) for i in range(n.value)]
 
 
 def coop_set_schedule(ctx, seed: int, p_kill: float, p_fork: float) -> None:

@@ -35,6 +35,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <condition_variable>
 #include <deque>
@@ -572,7 +573,7 @@ __device__ __forceinline__ uint32_t expand_range_bfs(const Params &p, const Inte
                                                      uint32_t wb, WarpStage &stage, Landing<MODE> &pf,
                                                      uint32_t &staged, bool &bad, uint32_t &nreach, uint64_t &ereach,
                                                      bool more, int32_t id, uint32_t GW, uint32_t &ch,
-                                                     uint32_t &ct) {
+                                                     uint32_t &ct, const volatile uint32_t *doom) {
   const unsigned lane = threadIdx.x & 31u;
   const uint32_t Etot = iv.edges;
   const uint32_t F = iv.count;
@@ -600,7 +601,28 @@ __device__ __forceinline__ uint32_t expand_range_bfs(const Params &p, const Inte
   }
   int sb = 0, sn = kStages - 1;
   uint32_t jn = kNoChunk;
+  // Kill point inside the chunk (KILL_CHUNK): once the CTA's doom watcher has seen the
+  // host's kill target take this CTA, a warp hands the rest of its chunk back (from a
+  // unit boundary, an indexed edge) and stops, so that the CTA leaves within about one
+  // iteration.
+  const bool handback = p.coop && p.kill_mode == KILL_CHUNK && MODE == MODE_BFS && id > 0;
+  uint32_t dm = handback ? *doom : 0u;  // read one iteration before it is tested
   for (uint32_t c = c0; c < E1; c += kIt, ci += kIt) {
+    if (handback && dm == iv.epoch && (c & (kIndexEdges - 1u)) == 0u) {
+      uint32_t pushed = 0u;
+      if (lane == 0) {
+        const uint32_t slot = atomicAdd(&p.ctl->ret_n, 1u);
+        if (slot < kRetCap) {
+          p.ctl->ret[slot] = ((unsigned long long)c << 32) | E1;
+          pushed = 1u;
+        }
+      }
+      if (__shfl_sync(kFull, pushed, 0) != 0u) {
+        cp_async_wait<0>();  // the copies in flight land before the buffers are left
+        return kNoChunk;
+      }
+      // the list is full: this iteration goes on (the next one tries again)
+    }
     if (more && lane == 0 && c + kIt >= E1 &&
         !(p.coop && p.kill_mode == KILL_CHUNK && doomed(ld_relaxed64(&p.ctl->kill_target), iv.epoch, id)))
       jn = GW + atomicAdd(&p.ctl->cursor.v, 1u);
@@ -630,6 +652,7 @@ __device__ __forceinline__ uint32_t expand_range_bfs(const Params &p, const Inte
     }
     sb = sb + 1 == kStages ? 0 : sb + 1;
     sn = sn + 1 == kStages ? 0 : sn + 1;
+    if (handback) dm = *doom;
   }
   return __shfl_sync(kFull, jn, 0);
 }
@@ -814,30 +837,49 @@ __device__ __forceinline__ bool sched_chunk(ChunkSched &sc, uint32_t k, uint32_t
 // without any search.  BFS expands queue iv.sel into the other one; SSSP queue xq (the
 // near queue, or a small pending queue whole) into the next pending queue.
 template <int MODE, int NW>
-__device__ void expand(const Params &p, const Interval &iv, int32_t id, WarpStage &stage, Landing<MODE> &pf) {
+__device__ void expand(const Params &p, const Interval &iv, int32_t id, WarpStage &stage, Landing<MODE> &pf,
+                       const volatile uint32_t *doom) {
   const unsigned lane = threadIdx.x & 31u;
   const uint32_t Etot = iv.edges;
   const uint32_t GW = (uint32_t)iv.M * NW;
   ChunkSched &sc = pf.sched;
   sched_init(sc, Etot, GW, MODE == MODE_SSSP ? kChunkUnitsMaxSssp : kChunkUnitsMax);
   uint32_t c0 = 0u, c1 = 0u;
-  if (!sched_chunk(sc, (uint32_t)id * NW + (threadIdx.x >> 5), Etot, GW, c0, c1)) return;
   const uint32_t *qx = MODE == MODE_SSSP ? queue(p.qx, sssp_xq(iv)) : iv.sel ? p.qx[1] : p.qx[0];
   const uint32_t out = iv.sel ^ 1u;
   uint32_t staged = 0u, nreach = 0u;
   uint32_t ch = 0u, ct = 0u;  // BFS claim ring: head and tail (warp-uniform)
   uint64_t ereach = 0ull;
   bool bad = false, ovf = false;
-  const bool more = sc.U > GW * sc.s;  // chunks beyond round 0 are claimed from the cursor
-  for (;;) {
+  const uint32_t gw = (uint32_t)id * NW + (threadIdx.x >> 5);
+  // BFS continuation interval: the returned ranges [lo, lo + n) of the level, range j for
+  // warp j mod GW; otherwise the chunks of the schedule
+  const uint32_t cont = MODE == MODE_BFS ? iv.cont : 0u;
+  const uint32_t lo = cont >> 16, n = cont & 0xFFFFu;
+  uint32_t j = gw;
+  auto next_range = [&]() -> bool {
+    while (j < n) {
+      const unsigned long long r = __ldcg(p.ctl->ret + lo + j);
+      j += GW;
+      c0 = (uint32_t)(r >> 32);
+      c1 = (uint32_t)r;
+      if (c0 < c1 && c1 <= Etot && (c0 & (kIndexEdges - 1u)) == 0u) return true;
+      bad = true;
+    }
+    return false;
+  };
+  bool have = cont ? next_range() : sched_chunk(sc, gw, Etot, GW, c0, c1);
+  const bool more = !cont && sc.U > GW * sc.s;  // chunks beyond round 0 are claimed from the cursor
+  while (have) {
     uint32_t k;
     if constexpr (MODE == MODE_SSSP)
       k = expand_range<MODE>(p, iv, c0, c1, qx[c0 / kIndexEdges], stage, pf, staged, bad, ovf, nreach, ereach, more,
                              id, GW);
     else
       k = expand_range_bfs<MODE>(p, iv, c0, c1, qx[c0 / kIndexEdges], stage, pf, staged, bad, nreach, ereach, more,
-                                 id, GW, ch, ct);
-    if (k == kNoChunk || !sched_chunk(sc, k, Etot, GW, c0, c1)) break;
+                                 id, GW, ch, ct, doom);
+    if (cont) have = next_range();
+    else have = k != kNoChunk && sched_chunk(sc, k, Etot, GW, c0, c1);
   }
   if constexpr (MODE != MODE_SSSP) {
     if (ct != ch) claim_batch(p, out, stage, staged, pf.cand, ch, ct - ch, (uint32_t)iv.level + 1u, bad, nreach,
@@ -927,6 +969,23 @@ __device__ __forceinline__ void scheduler_warp(const Params &p, const volatile i
     }
     if (ld_relaxed(&c->done) != 0u || ld_relaxed(&c->err) != 0u || *workers_left != 0) return;
     __nanosleep(200);
+  }
+}
+
+// The doom watcher of a BFS CTA other than the master (its otherwise idle 32nd warp, in
+// KILL_CHUNK mode): polls the host's kill target and records in shared memory the epoch
+// of the interval in which the target takes this CTA, so that the worker warps see it
+// with a shared-memory read per iteration and hand their chunks back.  Runs until the
+// CTA's workers have left or the traversal is over.
+__device__ __forceinline__ void doom_watcher(const Params &p, CtaShared &cs) {
+  const volatile Interval *iv = &cs.iv;
+  const volatile int32_t *left = &cs.workers_left;
+  volatile uint32_t *doom = &cs.doom;
+  for (;;) {
+    const uint32_t e = iv->epoch;
+    if (doomed(ld_relaxed64(&p.ctl->kill_target), e, cs.id)) *doom = e;
+    if (*left != 0 || ld_relaxed(&p.ctl->done) != 0u || ld_relaxed(&p.ctl->err) != 0u) return;
+    __nanosleep(256);
   }
 }
 
@@ -1098,9 +1157,9 @@ __device__ __forceinline__ void worker_loop(const Params &p, CtaShared &cs, Warp
       // the landing buffers are idle in a select interval: their first kHistBuckets words
       // hold the CTA's histogram
       if (sssp_select(iv)) select_interval<NW>(p, iv, id, reinterpret_cast<uint32_t *>(pfs), cs);
-      else expand<MODE, NW>(p, iv, id, stage, pf);
+      else expand<MODE, NW>(p, iv, id, stage, pf, &cs.doom);
     } else if constexpr (MODE != MODE_BARRIER) {
-      expand<MODE, NW>(p, iv, id, stage, pf);
+      expand<MODE, NW>(p, iv, id, stage, pf, &cs.doom);
     }
     if (!resizing_barrier<MODE, NW>(p, cs)) return;
   }
@@ -1123,11 +1182,15 @@ __device__ __forceinline__ void traverse_body(const Params &p, bool master, CtaS
     }
     cs.exit = active ? 0 : 1;
     cs.workers_left = 0;
+    cs.doom = 0u;
   }
   __syncthreads();
   if (cs.exit) return;
   if (threadIdx.x >= NW * 32) {
-    if (p.coop && cs.id == 0 && threadIdx.x == NW * 32) scheduler_warp<MODE, NW>(p, &cs.workers_left);
+    if (p.coop && threadIdx.x == NW * 32) {
+      if (cs.id == 0) scheduler_warp<MODE, NW>(p, &cs.workers_left);
+      else if (MODE == MODE_BFS && p.kill_mode == KILL_CHUNK) doom_watcher(p, cs);
+    }
     return;
   }
   // dynamic shared memory: NW enqueue stages, then NW landing buffers
@@ -1818,11 +1881,16 @@ struct coop_ctx {
   uint64_t sched_seed = 0;
   double p_kill = 0.0, p_fork = 0.0;
   double gather_us_max = 0.0;
+  // coop_request_resources records: {posted (us since coop_init), CTAs asked for, M when
+  // posted, M when granted, gather us, CTAs granted}; the latest kReqLog
+  std::chrono::steady_clock::time_point t_init = std::chrono::steady_clock::now();
+  std::deque<std::array<double, 6>> req_log;
 };
 
 namespace {
 
 thread_local char g_last_error[256] = "";
+constexpr size_t kReqLog = 4096;  // coop_request_resources records kept per context
 
 // Record a failing CUDA call (what + the runtime's error name and string) for
 // coop_last_cuda_error(); returns true when `e` is an error.
@@ -2243,17 +2311,37 @@ coop_status coop_request_resources(coop_ctx *c, int n, int timeout_us, int *n_fr
   if (!c || n < 1) return COOP_EINVAL;
   uint32_t target = 0;
   bool granted = false;
+  const auto t0 = std::chrono::steady_clock::now();
+  const int m_post = __atomic_load_n(&c->mbox->active, __ATOMIC_ACQUIRE);
   const coop_status st = post_kill(c, n, &target, &granted);
   if (st != COOP_OK) return st;
-  if (granted) {
-    if (n_freed) *n_freed = n;
-    return COOP_OK;
+  int got = n;
+  coop_status w = COOP_OK;
+  if (!granted) {
+    const auto deadline = t0 + std::chrono::microseconds(std::max(0, timeout_us));
+    w = wait_kill(c, target, n, timeout_us > 0, deadline, &got);
   }
-  int got = 0;
-  const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(std::max(0, timeout_us));
-  const coop_status w = wait_kill(c, target, n, timeout_us > 0, deadline, &got);
   if (n_freed) *n_freed = got;
+  const auto t1 = std::chrono::steady_clock::now();
+  const int m_grant = __atomic_load_n(&c->mbox->active, __ATOMIC_ACQUIRE);
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->req_log.push_back({std::chrono::duration<double, std::micro>(t0 - c->t_init).count(), (double)n,
+                        granted ? 0.0 : (double)m_post, granted ? 0.0 : (double)m_grant,
+                        std::chrono::duration<double, std::micro>(t1 - t0).count(), (double)got});
+  if (c->req_log.size() > kReqLog) c->req_log.pop_front();
   return w;
+}
+
+coop_status coop_get_request_log(coop_ctx *c, double *out, int cap, int *n, int clear) {
+  if (!c || !n || cap < 0 || (cap > 0 && !out)) return COOP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  const int take = std::min<int>(cap, (int)c->req_log.size());
+  const size_t first = c->req_log.size() - (size_t)take;  // the latest `take` records
+  for (int i = 0; i < take; ++i)
+    for (int j = 0; j < 6; ++j) out[6 * (size_t)i + j] = c->req_log[first + (size_t)i][j];
+  *n = take;
+  if (clear) c->req_log.clear();
+  return COOP_OK;
 }
 
 coop_status coop_release(coop_ctx *c, int n) {

@@ -62,6 +62,12 @@ constexpr uint32_t kChunkUnitsMaxSssp = 4;  // SSSP: 1..4 units
 // bulk are far slower than loads).  On smaller frontiers the read is one more dependent
 // round trip on the level's critical path, and the claim goes straight to the atomic.
 constexpr uint32_t kPrecheckEdges = 65536;
+// BFS: a CTA that the host's kill target dooms in the middle of a chunk hands the rest of
+// the chunk back (the warp stops after its current iteration) into a list of returned
+// edge ranges in the control block; the release turns them into a continuation interval
+// of the same level.  kRetCap ranges per level at most (beyond that a doomed warp
+// finishes its chunk).
+constexpr uint32_t kRetCap = 32768;
 // p-sssp: a flagged row of at least kTopoHeavy edges is not relaxed by the one warp whose
 // vertex stripe holds it but listed, as chunks of kTopoChunk edges, by the update interval
 // that flagged it; the relax interval deals the chunks out over every warp of the grid.
@@ -121,6 +127,9 @@ struct Interval {
   // next round's sel ^ 1; select is 1 in a round's select interval, 0 in an expand
   // interval, which expands queue xq (kNearQueue, or the pending queue whole)
   uint32_t sssp;
+  // BFS continuation interval (nonzero): the returned ranges [lo, lo + n) of the level's
+  // edge space to expand, as lo << 16 | n
+  uint32_t cont;
 };
 
 __host__ __device__ constexpr uint32_t sssp_word(uint32_t round, uint32_t select, uint32_t xq) {
@@ -187,8 +196,11 @@ struct Ctl {
   // the next round's histogram base
   alignas(128) uint32_t dmin;
   uint32_t pad_s[31];
+  alignas(128) uint32_t ret_n;  // BFS: edge ranges handed back in the current level
+  uint32_t pad_r2[31];
   alignas(128) unsigned long long slot[kMaxCtas];  // admission records, by ticket % kMaxCtas
   LogRec log[kLogCap];
+  unsigned long long ret[kRetCap];  // BFS: returned ranges, first edge << 32 | end (not cleared)
 };
 
 // Host <-> device mailbox in mapped pinned host memory.
@@ -200,7 +212,8 @@ struct alignas(128) Mailbox {
   uint32_t freed;     // device -> host: cumulative requested CTAs that have left
   int32_t err;        // device -> host: sticky error of the current run
   uint32_t run_done;  // device -> host: id of the last run that finished
-  uint32_t pad1[29];
+  int32_t active;     // device -> host: active CTAs (M) after the latest resizing barrier
+  uint32_t pad1[28];
   int32_t levels, barriers, kills, forks, min_active, max_active, initial_active, status;
   int32_t ctas_launched, pad2;
   unsigned long long edges_scanned, frontier_total;
@@ -262,6 +275,8 @@ struct CtaShared {
   int32_t exit;
   int32_t workers_left;  // set when this CTA's worker warps have left (bounds the poller)
   int32_t leave;         // this CTA leaves at the current barrier (host kill)
+  uint32_t doom;         // BFS: epoch of the interval in which the host's kill target dooms
+                         // this CTA (set by the CTA's doom watcher warp)
 };
 
 // ---------------------------------------------------------------- PTX wrappers
@@ -449,6 +464,7 @@ __device__ __forceinline__ uint32_t precheck_hint(uint32_t edges) { return edges
 // waiter reads them, and this thread's next arrival (a release) orders them before the
 // next releaser's loads.
 struct Books {
+  int32_t m_after;  // the new interval's M, for the host mailbox
   uint32_t admitted;
   int32_t barriers, kills, forks, min_active, max_active;
   unsigned long long edges_scanned, frontier_total;
@@ -496,6 +512,7 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
   const unsigned long long es0 = c->edges_scanned, ft0 = c->frontier_total, t_start = c->t_start;
   uint32_t log_n = c->log_n;
   const uint32_t err = ld_relaxed(&c->err);
+  const uint32_t ret_raw = MODE == MODE_BFS ? ld_relaxed(&c->ret_n) : 0u;
   const uint32_t R = p.coop ? ld_relaxed(&c->join_ticket.v) : 0u;
   const uint64_t now = gtime();
   int32_t Mmid = M;
@@ -509,8 +526,19 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
   Interval nxt = cur;
   nxt.epoch = cur.epoch + 1u;
   nxt.level = cur.level + 1;
+  // BFS: ranges handed back by doomed CTAs and not yet expanded open a continuation
+  // interval of the same level
+  const uint32_t ret_n = min(ret_raw, kRetCap);
+  const uint32_t ret_done = (cur.cont >> 16) + (cur.cont & 0xFFFFu);
+  const bool cont = MODE == MODE_BFS && err == 0u && ret_n > ret_done;
   uint32_t count, edges;
-  if (MODE == MODE_BARRIER) {
+  if (cont) {
+    nxt.level = cur.level;
+    nxt.cont = ret_done << 16 | (ret_n - ret_done);
+    count = cur.count;
+    edges = cur.edges;
+    c->cursor.v = 0u;
+  } else if (MODE == MODE_BARRIER) {
     count = (cur.level + 1 < p.n_barriers) ? 1u : 0u;
     edges = 0u;
   } else if (MODE == MODE_PSSSP) {
@@ -548,6 +576,10 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
     c->qctr[cur.sel] = 0ull;  // the finished input queue becomes the next output queue
     c->cursor.v = 0u;
     nxt.sel = out;
+    if (MODE == MODE_BFS) {
+      nxt.cont = 0u;
+      if (ret_n) st_relaxed(&c->ret_n, 0u);
+    }
   }
   nxt.count = count;
   nxt.edges = edges;
@@ -590,10 +622,11 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
   nxt.M = Mn;
   nxt.doom = (uint32_t)Mmid;
   if (simple) st_relaxed64(&c->live, (unsigned long long)(uint32_t)Mn << 32);
-  nxt.precheck = precheck_hint(edges);
+  if (!cont) nxt.precheck = precheck_hint(edges);
   c->iv = nxt;
   if (nxt.done) st_release(&c->done, 1u);  // after the admission slots (join_enter relies on it)
 
+  bk.m_after = Mn;
   bk.admitted = A + (uint32_t)k;
   bk.barriers = barriers;
   bk.kills = kills0 + Wmid + W;
@@ -602,7 +635,7 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
   bk.max_active = max(maxa, Mn);
   // edges and vertices of the frontiers the traversal expands (SSSP: not the pending
   // queues that a select interval splits)
-  const bool expands = !nxt.done && (MODE != MODE_SSSP || !sssp_select(nxt));
+  const bool expands = !nxt.done && !cont && (MODE != MODE_SSSP || !sssp_select(nxt));
   bk.edges_scanned = expands ? es0 + edges : es0;
   bk.frontier_total = expands ? ft0 + count : ft0;
   // every barrier while the first half of the trace has room, resize events always
@@ -632,6 +665,7 @@ __device__ __forceinline__ void release_books(const Params &p, const Books &bk) 
   if (bk.has_kill) c->log[ln++] = bk.kill_rec;
   if (bk.has_rec) c->log[ln++] = bk.rec;
   c->log_n = ln;
+  if (p.coop) st_sys((uint32_t *)&p.mbox->active, (uint32_t)bk.m_after);
   if (bk.status != 1) publish_stats(p, bk.status);
 }
 
@@ -802,6 +836,7 @@ __device__ __forceinline__ void master_enter(const Params &p, CtaShared &cs) {
   iv.precheck = precheck_hint(edges);
   iv.base = 0u;
   iv.sssp = sssp_word(0u, 0u, 0u);  // SSSP round 0 expands the source's pending queue whole
+  iv.cont = 0u;
   c->dmin = 0xFFFFFFFFu;
   c->admitted = (uint32_t)k;
   c->live = (unsigned long long)(uint32_t)iv.M << 32;
@@ -819,6 +854,7 @@ __device__ __forceinline__ void master_enter(const Params &p, CtaShared &cs) {
     publish_stats(p, (int)e);
   }
   st_release(&c->epoch.v, 1u);
+  if (p.coop) st_sys((uint32_t *)&p.mbox->active, (uint32_t)iv.M);
   cs.iv = iv;
   cs.id = 0;
 }

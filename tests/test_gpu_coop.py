@@ -342,3 +342,150 @@ def test_full_size_rmat22_bfs_under_schedules(ctx):
         assert_same(lv, ref, f"rmat22 bfs under schedule {seed}")
         assert st.kills > 0 and st.forks > 0, (seed, st.kills, st.forks)
         _replay(ctx, st)
+
+
+@pytest.mark.parametrize("name,period_ms,task_ms,share", [("light", 70.0, 3.0, 4), ("medium", 40.0, 3.0, 4),
+                                                            ("heavy", 40.0, 10.0, 2)])
+def test_traversals_bit_exact_under_table3_classes(ctx, name, period_ms, task_ms, share):
+    """Sec. 5.5 / Table 3's workload classes: back-to-back BFS traversals while a
+    non-cooperative task (saxpy launches sized to run about task_ms alone) takes N/share
+    CTAs every period_ms and gives them back.  Every traversal's levels equal the
+    oracle's, compared on the device after each one, and every task got its CTAs."""
+    import torch
+    g = gg.rmat(18, 16, seed=18)
+    src = gg.max_out_degree_vertex(g)
+    dg = DevGraph(g)
+    ref = torch.from_numpy(oracle.bfs(g, src)).to(dg.device)
+    lv = dg.empty()
+    N = coop.coop_query(ctx)["max_ctas"]
+    k = N // share
+    x = torch.rand(1 << 22, device=dg.device)
+    y = torch.rand(1 << 22, device=dg.device)
+    cs = torch.cuda.Stream(device=dg.device, priority=-1)
+    t0 = time.perf_counter()
+    coop.coop_saxpy(k, 2.0, x, y, stream=cs)
+    cs.synchronize()
+    reps = max(1, int(task_ms / max((time.perf_counter() - t0) * 1e3, 0.01)))
+    got_all, stop = [], threading.Event()
+
+    def ticker():
+        nxt = time.perf_counter()
+        while not stop.is_set():
+            got = coop.coop_request_resources(ctx, k, timeout_us=2_000_000)
+            got_all.append(got)
+            for _ in range(reps):
+                coop.coop_saxpy(k, 2.0, x, y, stream=cs)
+            cs.synchronize()
+            coop.coop_release(ctx, got)
+            nxt += period_ms / 1e3
+            time.sleep(max(0.0, nxt - time.perf_counter()))
+
+    stream = torch.cuda.Stream(device=dg.device)
+    th = threading.Thread(target=ticker)
+    th.start()
+    n, bad = 0, 0
+    t0 = time.perf_counter()
+    try:
+        while time.perf_counter() - t0 < 0.5:
+            coop.coop_bfs(ctx, dg.csr, src, lv, stream=stream)
+            stream.synchronize()
+            bad += 0 if torch.equal(lv, ref) else 1
+            n += 1
+    finally:
+        stop.set()
+        th.join()
+    assert coop.coop_sync(ctx) == coop.COOP_OK
+    assert n > 10 and bad == 0, (name, n, bad)
+    assert len(got_all) >= 3 and all(got == k for got in got_all), (name, got_all)
+
+
+def test_request_log_records_every_request(ctx):
+    """coop_get_request_log: one record per coop_request_resources call, in order, with
+    the CTAs asked for and granted, and M as the device published it (0 for a request
+    granted at once with no traversal in flight, else within [1, N])."""
+    import torch
+    g = gg.rmat(17, 16, seed=3)
+    src = gg.max_out_degree_vertex(g)
+    dg = DevGraph(g)
+    lv = dg.empty()
+    N = coop.coop_query(ctx)["max_ctas"]
+    coop.coop_get_request_log(ctx, clear=True)
+    got = coop.coop_request_resources(ctx, 5)
+    coop.coop_release(ctx, got)
+    asks, stop = [], threading.Event()
+
+    def ticker():
+        while not stop.is_set():
+            n = 1 + len(asks) % (N // 2)
+            got = coop.coop_request_resources(ctx, n, timeout_us=2_000_000)
+            asks.append((n, got))
+            coop.coop_release(ctx, got)
+            time.sleep(0.0003)
+
+    stream = torch.cuda.Stream()
+    th = threading.Thread(target=ticker)
+    th.start()
+    try:
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 0.3:
+            coop.coop_bfs(ctx, dg.csr, src, lv, stream=stream)
+        stream.synchronize()
+    finally:
+        stop.set()
+        th.join()
+    coop.coop_sync(ctx)
+    log = coop.coop_get_request_log(ctx, clear=True)
+    assert len(log) == 1 + len(asks)
+    assert log[0]["n_ctas"] == 5 and log[0]["granted"] == 5 and log[0]["active_at_post"] == 0
+    assert [r["t_us"] for r in log] == sorted(r["t_us"] for r in log)
+    for r, (n, got) in zip(log[1:], asks):
+        assert r["n_ctas"] == n and r["granted"] == got == n and r["gather_us"] >= 0
+        for m in (r["active_at_post"], r["active_at_grant"]):
+            assert m == 0 or 1 <= m <= N
+    assert any(r["active_at_post"] > 0 for r in log[1:]), "no request landed during a traversal"
+    assert coop.coop_get_request_log(ctx) == []
+    assert coop.coop_sync(ctx) == coop.COOP_OK
+    np.testing.assert_array_equal(lv.cpu().numpy(), oracle.bfs(g, src))
+
+
+def test_chunks_handed_back_mid_level_are_expanded_in_a_continuation(ctx):
+    """Host requests that arrive in the middle of a wide level: the doomed CTAs hand the
+    rest of their chunks back and leave within about one iteration; the returned ranges
+    are expanded in a continuation interval of the same level (more barriers than levels).
+    Every traversal's levels equal the oracle's, and every request is granted."""
+    import torch
+    g = gg.rmat(20, 16, seed=20)
+    src = gg.max_out_degree_vertex(g)
+    dg = DevGraph(g)
+    ref = torch.from_numpy(oracle.bfs(g, src)).to(dg.device)
+    lv = dg.empty()
+    N = coop.coop_query(ctx)["max_ctas"]
+    stop, grants = threading.Event(), []
+
+    def ticker():
+        i = 0
+        while not stop.is_set():
+            n = (N // 2, N // 4, N - 1, 3)[i % 4]
+            got = coop.coop_request_resources(ctx, n, timeout_us=2_000_000)
+            grants.append((n, got))
+            time.sleep(0.00002)
+            coop.coop_release(ctx, got)
+            i += 1
+
+    th = threading.Thread(target=ticker)
+    th.start()
+    runs, cont_runs, bad = 0, 0, 0
+    try:
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 1.0:
+            st = coop.coop_bfs(ctx, dg.csr, src, lv, stats=True)
+            bad += 0 if torch.equal(lv, ref) else 1
+            cont_runs += st.barriers > st.levels
+            runs += 1
+    finally:
+        stop.set()
+        th.join()
+    assert coop.coop_sync(ctx) == coop.COOP_OK
+    assert bad == 0, (bad, runs)
+    assert all(got == n for n, got in grants) and len(grants) > 20
+    assert cont_runs > 0, "no traversal expanded a returned range"
