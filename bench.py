@@ -54,8 +54,8 @@ WORKLOADS = {
 # workload, from the ncu captures summarised in profiles/; an entry is used only while
 # the kernel sources still have the digest it was taken on (otherwise null).
 TRAFFIC = {
-    "rmat20-sssp": {"sources_sha": "cf783cdda4306f4f", "bytes": 373181696},
-    "rmat22-bfs": {"sources_sha": "cf783cdda4306f4f", "bytes": 391909888},
+    "rmat22-bfs": {"sources_sha": "96d5fe9e7f2cb158", "bytes": 391670016},
+    "rmat20-sssp": {"sources_sha": "96d5fe9e7f2cb158", "bytes": 205054720},
 }
 
 
