@@ -1019,19 +1019,24 @@ def batched(coop, ctx, dev, stream, flush, n_inst=64, seed=3, steps=5):
     # parity of the batched results (run once more, then compare every job)
     run()
     torch.cuda.synchronize(dev)
-    exact = 0
+    exact, algo = 0, 0
     for g, w, src, lv, dist in outs:
         l = lv.cpu().numpy()
         d = dist.cpu().numpy().view(np.uint32)
         exact += int(np.array_equal(l, oracle.bfs(g, src))) + int(np.array_equal(d, oracle.dijkstra(g, w, src)))
         deg = np.diff(g.row_off.astype(np.int64))
-        es_total += int(deg[l >= 0].sum()) * 2  # BFS and SSSP reach the same vertices
+        vr, es = int((l >= 0).sum()), int(deg[l >= 0].sum())
+        es_total += es * 2  # BFS and SSSP reach the same vertices
+        algo += algorithmic_bytes(g.num_vertices, vr, es, "bfs") + algorithmic_bytes(g.num_vertices, vr, es, "sssp")
+    hbm, _ = peaks()
     return {"instances": int(n_inst), "jobs": len(jobs), "scales": [int(x) for x in scales],
             "edges_total": int(edges_total), "E_s_total": int(es_total),
             "batch_ms": round(ms_batch, 3), "one_launch_per_job_ms": round(ms_single, 3),
             "gteps_batched": round(es_total / (ms_batch / 1e3) / 1e9, 3),
             "gteps_one_per_job": round(es_total / (ms_single / 1e3) / 1e9, 3),
             "speedup": round(ms_single / ms_batch, 3), "graph_captured": True,
+            # every job's algorithmic bytes over the batch's time, against the HBM peak
+            "algorithmic_bytes": int(algo), "hbm_frac": round(algo / (ms_batch / 1e3) / 1e9 / hbm, 4),
             "tuned_ctas_total": int(sum(ctas)), "tune_s": round(tune_s, 2),
             "jobs_bit_exact": exact, "all_ok": all(s.status == 0 for s in stats)}
 

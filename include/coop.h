@@ -278,7 +278,8 @@ typedef struct coop_batch coop_batch; /* opaque, library-owned */
 coop_status coop_batch_create(coop_ctx *ctx, const coop_job *jobs, int n_jobs, coop_batch **out);
 
 /* Set the blocks of every job (ctas[i] >= 1; the sum may exceed the resident capacity:
- * jobs whose blocks are not resident yet start when earlier jobs free their SMs). */
+ * jobs whose blocks are not resident yet start when earlier jobs free their SMs).  Waits
+ * for the batch's last run, on whatever stream, before it rewrites the job table. */
 coop_status coop_batch_set_ctas(coop_batch *b, const int32_t *ctas);
 
 /*
@@ -320,8 +321,12 @@ typedef struct {
 
 /*
  * Create a server on `device` with `slots` concurrent query slots (each a context of its
- * own).  hbm_budget_bytes (0 = no limit) bounds the scratch the slots may hold for the
- * registered graphs; coop_server_add_graph fails with COOP_ENOMEM beyond it.
+ * own).  hbm_budget_bytes (0 = no limit) bounds the device memory of the registered
+ * graphs (CSR and weights) plus the scratch every slot holds for the largest of them;
+ * coop_server_add_graph fails with COOP_ENOMEM beyond it.  Since every slot is sized for
+ * every graph before the first query, admission while serving is by free slot: a query
+ * that finds a slot free runs within the budget.  Query outputs are the caller's memory
+ * and are not counted.
  */
 coop_status coop_server_create(int device, int slots, size_t hbm_budget_bytes, coop_server **out);
 

@@ -2517,6 +2517,8 @@ struct coop_batch {
   cudaGraphExec_t graph = nullptr;
   bool graph_valid = false;
   cudaStream_t capture = nullptr;  // private stream the graph is recorded on
+  cudaEvent_t ran = nullptr;       // recorded after every run: the job table is in use until then
+  bool any_run = false;
   int64_t max_V = 0;
 };
 
@@ -2571,6 +2573,8 @@ coop_status batch_layout(coop_batch *b) {
     at += (uint32_t)b->ctas[j];
   }
   b->total = at;
+  // a run still in flight (on any stream) reads the table: let it finish first
+  if (b->any_run && cuda_failed(cudaEventSynchronize(b->ran), "batch run")) return COOP_ECUDA;
   if (cuda_failed(cudaMemcpy(b->d_params, ps.data(), sizeof(Params) * n, cudaMemcpyHostToDevice), "batch table") ||
       cuda_failed(cudaMemcpy(b->d_first, first.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice), "batch table"))
     return COOP_ECUDA;
@@ -2637,7 +2641,8 @@ coop_status coop_batch_create(coop_ctx *c, const coop_job *jobs, int n, coop_bat
     coop_batch_destroy(b);
     return st;
   };
-  if (cuda_failed(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking), "capture stream"))
+  if (cuda_failed(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking), "capture stream") ||
+      cuda_failed(cudaEventCreateWithFlags(&b->ran, cudaEventDisableTiming), "batch event"))
     return fail(COOP_ECUDA);
   if (cuda_failed(cudaMalloc(&b->scratch, std::max<size_t>(off[n], 256)), "batch scratch") ||
       cuda_failed(cudaMalloc((void **)&b->d_params, sizeof(Params) * n), "batch table") ||
@@ -2704,6 +2709,8 @@ coop_status coop_batch_run(coop_batch *b, coop_stream stream, int use_graph) {
   cudaStream_t s = (cudaStream_t)stream;
   if (!use_graph) {
     batch_enqueue(b, s);
+    cudaEventRecord(b->ran, s);
+    b->any_run = true;
     return cuda_failed(cudaGetLastError(), "batch launch") ? COOP_ECUDA : COOP_OK;
   }
   if (!b->graph_valid) {
@@ -2724,7 +2731,10 @@ coop_status coop_batch_run(coop_batch *b, coop_stream stream, int use_graph) {
     if (cuda_failed(ie, "graph instantiate")) return COOP_ECUDA;
     b->graph_valid = true;
   }
-  return cuda_failed(cudaGraphLaunch(b->graph, s), "graph launch") ? COOP_ECUDA : COOP_OK;
+  if (cuda_failed(cudaGraphLaunch(b->graph, s), "graph launch")) return COOP_ECUDA;
+  cudaEventRecord(b->ran, s);
+  b->any_run = true;
+  return cuda_failed(cudaGetLastError(), "batch event") ? COOP_ECUDA : COOP_OK;
 }
 
 coop_status coop_batch_tune(coop_batch *b, coop_stream stream, int32_t *ctas_out) {
@@ -2749,6 +2759,8 @@ coop_status coop_batch_tune(coop_batch *b, coop_stream stream, int32_t *ctas_out
         cudaEventRecord(e0, s);
         batch_enqueue(b, s);
         cudaEventRecord(e1, s);
+        cudaEventRecord(b->ran, s);
+        b->any_run = true;
         if (cuda_failed(cudaEventSynchronize(e1), "tune run")) {
           st = COOP_ECUDA;
           break;
@@ -2806,6 +2818,7 @@ coop_status coop_batch_destroy(coop_batch *b) {
   cudaDeviceSynchronize();
   if (b->graph) cudaGraphExecDestroy(b->graph);
   if (b->capture) cudaStreamDestroy(b->capture);
+  if (b->ran) cudaEventDestroy(b->ran);
   if (b->scratch) cudaFree(b->scratch);
   if (b->d_params) cudaFree(b->d_params);
   if (b->d_first) cudaFree(b->d_first);
@@ -2833,6 +2846,7 @@ struct coop_server {
   int N = 0;           // CTAs of the GPU (one per SM)
   int min_share = 1;   // a running query never drops below this many CTAs
   size_t budget = 0, per_slot = 0;
+  size_t resident = 0;  // device bytes of the registered graphs (CSR and weights)
   struct Slot {
     coop_ctx *ctx = nullptr;
     cudaStream_t stream = nullptr;
@@ -3010,10 +3024,14 @@ coop_status coop_server_add_graph(coop_server *sv, const coop_csr *g, const uint
   std::lock_guard<std::mutex> lk(sv->mu);
   if (sv->started) return COOP_EBUSY;  // graphs are registered before the first query
   // every slot must be able to serve the graph: size its scratch now, before serving,
-  // since an allocation while queries run would wait for them
-  const size_t per = (size_t)g->num_vertices * 4 * 8 + (size_t)(g->num_edges / kIndexEdges + 2) * 8 + (1u << 20);
+  // since an allocation while queries run would wait for them.  The budget covers every
+  // slot's scratch (bitmap, three queues of three words per vertex, the packed distance
+  // words, three chunk indexes) and the graphs registered so far.
+  const size_t V = (size_t)g->num_vertices, E = (size_t)g->num_edges;
+  const size_t per = V * 4 * 11 + (V + 31) / 32 * 4 + (E / kIndexEdges + 2) * 4 * 3 + (1u << 20);
+  const size_t graph = (V + 1) * 4 + E * 4 + (d_weights ? E * 4 : 0);
   const size_t per_slot = std::max(sv->per_slot, per);
-  if (sv->budget && per_slot * sv->slots.size() > sv->budget) return COOP_ENOMEM;
+  if (sv->budget && per_slot * sv->slots.size() + sv->resident + graph > sv->budget) return COOP_ENOMEM;
   for (auto &sl : sv->slots) {
     DeviceGuard guard(sv->device);
     std::lock_guard<std::mutex> lk2(sl.ctx->mu);
@@ -3021,6 +3039,7 @@ coop_status coop_server_add_graph(coop_server *sv, const coop_csr *g, const uint
     if (st != COOP_OK) return st;
   }
   sv->per_slot = per_slot;
+  sv->resident += graph;
   sv->graphs.push_back({*g, d_weights});
   *graph_id = (int)sv->graphs.size() - 1;
   return COOP_OK;
