@@ -77,7 +77,9 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region: the
+    sampler is running (its first sample in) before the region starts, samples every
+    20 ms, and only samples taken from the region's start on are summarised."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -86,25 +88,31 @@ class ClockSampler:
     def __init__(self, device_index: int):
         self.dev = device_index
         self.proc = None
-        self.lines = []
+        self.lines = []  # (host time, line)
+        self.t0 = 0.0
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
+            t_wait = time.perf_counter()
+            while not self.lines and time.perf_counter() - t_wait < 3.0 and self.proc.poll() is None:
+                time.sleep(0.005)
         except Exception:
             self.proc = None
+        self.t0 = time.perf_counter()
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
     def __exit__(self, *a):
         if self.proc:
+            time.sleep(0.03)  # one more sample after the region
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -114,7 +122,8 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        inside = [ln for t, ln in self.lines if t >= self.t0] or [ln for _, ln in self.lines[-1:]]
+        for ln in inside:
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -128,7 +137,8 @@ class ClockSampler:
                     reasons.add(n)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": statistics.median(sm), "sm_min_mhz": min(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
 
 
 HEADLINE = "rmat22-bfs"
@@ -436,13 +446,29 @@ def random_schedules(coop, ctx, csr, src, lv, ref, stream, es, seeds=(0, 1, 2, 3
         st = coop.coop_bfs(ctx, csr, src, lv, stream=stream, stats=True)
         dt = time.perf_counter() - t0
         res.append({"seed": seed, "bit_exact": bool(np.array_equal(lv.cpu().numpy(), ref)), "kills": st.kills,
-                    "forks": st.forks, "min_active": st.min_active, "kernel_us": round(st.kernel_us, 1),
+                    "forks": st.forks, "joined": st.joined, "min_active": st.min_active,
+                    "kernel_us": round(st.kernel_us, 1),
                     "gteps_kernel": round(es / (st.kernel_us / 1e6) / 1e9, 2), "host_ms": round(dt * 1e3, 2)})
     coop.coop_set_schedule(ctx, 0, 0.0, 0.0)
     return res
 
 
-def corunner(coop, ctx, dev, csr, src, lv, stream, period_s=1.0 / 60.0, duration_s=1.5, work=None):
+class gil_handover:
+    """The co-runner's host thread and the thread launching traversals share one Python
+    interpreter; a thread coming back from a library call waits for the other to give up
+    the interpreter lock, by default up to 5 ms.  While a co-runner is timed the hand-over
+    interval is 10 us, so that the latency measured is the system's, not the harness's
+    (a co-runner in its own process or native thread has no such wait)."""
+
+    def __enter__(self):
+        self.old = sys.getswitchinterval()
+        sys.setswitchinterval(1e-5)
+
+    def __exit__(self, *exc):
+        sys.setswitchinterval(self.old)
+
+
+def corunner(coop, ctx, dev, csr, src, lv, stream, period_s=1.0 / 60.0, duration_s=3.0, work=None):
     """Cooperative multitasking: a periodic fp32 saxpy over 64 MB (x and y, 16.7 ms period)
     that claims half the SMs from back-to-back R-MAT 22 BFS traversals.
 
@@ -497,19 +523,22 @@ def corunner(coop, ctx, dev, csr, src, lv, stream, period_s=1.0 / 60.0, duration
 
     th = threading.Thread(target=ticker)
     coop.coop_get_request_log(ctx, clear=True)
-    t0 = time.perf_counter()
-    th.start()
-    n_co = 0
-    while time.perf_counter() - t0 < duration_s:
-        coop.coop_bfs(ctx, csr, src, lv, stream=stream)
-        n_co += 1
-    stream.synchronize()
-    per_co = (time.perf_counter() - t0) / n_co
-    stop.set()
-    th.join()
+    with gil_handover():
+        t0 = time.perf_counter()
+        th.start()
+        n_co = 0
+        while time.perf_counter() - t0 < duration_s:
+            coop.coop_bfs(ctx, csr, src, lv, stream=stream)
+            n_co += 1
+        stream.synchronize()
+        per_co = (time.perf_counter() - t0) / n_co
+        stop.set()
+        th.join()
     coop.coop_sync(ctx)
     reqs = coop.coop_get_request_log(ctx, clear=True)
     slowest = sorted(reqs, key=lambda r: -r["gather_us"])[:3]
+    dev_gather = [r["gather_us"] / 1e3 for r in reqs if r["active_at_post"] > 0]
+    run = [l - g for l, g in zip(lat, gat)]
 
     def pct(v, q):
         v = sorted(v)
@@ -520,6 +549,10 @@ def corunner(coop, ctx, dev, csr, src, lv, stream, period_s=1.0 / 60.0, duration
             "solo_ms_p50": pct(solo, 0.5), "solo_ms_p99": pct(solo, 0.99),
             "p99_vs_solo": round(pct(lat, 0.99) / pct(solo, 0.99), 3),
             "gather_ms_p50": pct(gat, 0.5), "gather_ms_p99": pct(gat, 0.99),
+            # the library's own clock around the gather (no interpreter), and the rest of a
+            # job: the saxpy on the lent SMs beside the traversal, launch and synchronise
+            "gather_ms_lib_p50": pct(dev_gather or [0.0], 0.5), "gather_ms_lib_p99": pct(dev_gather or [0.0], 0.99),
+            "run_ms_p50": pct(run, 0.5), "run_ms_p99": pct(run, 0.99),
             "deadline_ms": 2.0, "deadline_met_frac": round(sum(l <= 2.0 for l in lat) / max(1, len(lat)), 4),
             "traversal_ms_alone": round(per_alone * 1e3, 4), "traversal_ms_corun": round(per_co * 1e3, 4),
             "coop_slowdown": round(per_co / per_alone, 4),
@@ -708,9 +741,12 @@ def table3(coop, ctx, dev, stream, csr, src, lv, ref, duration_s=1.0, classes=TA
         reps = max(1, int(round(E / max(one, 1e-3))))
         D = statistics.median(job_alone(k, reps) for _ in range(5))
 
+        gather = []
+
         def coop_job():
             t0 = time.perf_counter()
             got = coop.coop_request_resources(ctx, k, timeout_us=2_000_000)
+            gather.append((time.perf_counter() - t0) * 1e3)
             for _ in range(reps):
                 coop.coop_saxpy(k, 2.0, x, y, stream=cs)
             cs.synchronize()
@@ -721,14 +757,19 @@ def table3(coop, ctx, dev, stream, csr, src, lv, ref, duration_s=1.0, classes=TA
         def plain_job():
             return job_alone(k, reps)
 
+        coop.coop_get_request_log(ctx, clear=True)
         per_c, lat_c, per_task_c, ok_c = corun(trav_coop, coop_job, P)
         coop.coop_sync(ctx)
+        reqs = coop.coop_get_request_log(ctx, clear=True)
+        slowest = max(reqs, key=lambda r: r["gather_us"]) if reqs else {}
         per_p, lat_p, per_task_p, ok_p = corun(trav_plain, plain_job, P)
         rows.append({
             "class": name, "period_ms": P, "task_ms": round(D, 3), "task_ctas": k, "task_launches": reps,
             "model_P_over_P_minus_D": round(P / (P - D), 3),
             "coop_slowdown": round(per_c / alone_coop, 3), "no_coop_slowdown": round(per_p / alone_plain, 3),
             "coop_task_latency_ms_p50": pct(lat_c, 0.5), "coop_task_latency_ms_p99": pct(lat_c, 0.99),
+            "coop_task_latency_ms_max": pct(lat_c, 1.0), "coop_gather_ms_max": pct(gather or [0.0], 1.0),
+            "slowest_request": {kk: round(v, 1) for kk, v in slowest.items()},
             "no_coop_task_latency_ms_p99": pct(lat_p, 0.99),
             "coop_task_period_ms": round(per_task_c, 2), "no_coop_task_period_ms": round(per_task_p, 2),
             "coop_deadline_met_frac": round(sum(l <= P for l in lat_c) / max(1, len(lat_c)), 3),
@@ -795,7 +836,7 @@ def occupancy_trace(coop, ctx, dev, stream, period_s=0.0005, runs=40):
         dwell = {}
         for r in log:
             dwell[r[5]] = dwell.get(r[5], 0) + 1
-        out[name] = {"N": N, "barriers": st.barriers, "kills": st.kills, "forks": st.forks,
+        out[name] = {"N": N, "barriers": st.barriers, "kills": st.kills, "forks": st.forks, "joined": st.joined,
                      "min_active": st.min_active, "kernel_us": round(st.kernel_us, 1),
                      "trace_t_us_M": trace[:200], "barriers_at_M": dict(sorted(dwell.items()))}
         del ro, col, lv
@@ -1260,8 +1301,13 @@ def secondary(coop, ctx, dev, stream, flush, args, head):
                               "gteps": round(es / (ms / 1e3) / 1e9, 3), "hbm_frac": round(B / (kus / 1e6) / 1e9 / hbm, 4),
                               "baseline_kernel_us": round(kusb, 2), "coop_overhead": round(kus / kusb, 4)}}
         res["bfs_rmat22_schedules"] = random_schedules(coop, ctx, csr, src, lv, lvh, stream, es)
-        res["corunner"] = corunner(coop, ctx, dev, csr, src, lv, stream, work=(es, B, hbm))
-        res["table3"] = table3(coop, ctx, dev, stream, csr, src, lv, lvh)
+        # each with the clocks seen while it ran: a throttling episode shows up beside it
+        with ClockSampler(dev.index or 0) as ck:
+            res["corunner"] = corunner(coop, ctx, dev, csr, src, lv, stream, work=(es, B, hbm))
+        res["corunner"]["clocks"] = ck.summary()
+        with ClockSampler(dev.index or 0) as ck:
+            res["table3"] = table3(coop, ctx, dev, stream, csr, src, lv, lvh)
+        res["table3"]["clocks"] = ck.summary()
         return res
 
     def grid():

@@ -85,7 +85,9 @@ typedef struct {
     int32_t initial_active; /* M after the entry barrier */
     int32_t status;         /* coop_status of the run */
     int32_t ctas_launched;  /* CTAs launched for the run: main grid + every forked CTA */
-    int32_t reserved;
+    int32_t joined;         /* of forks, the CTAs that joined a BFS level while it ran (they
+                               take chunks from the level's shared cursor) rather than
+                               waiting for the next barrier */
     int64_t edges_scanned;  /* sum of out-degrees over every expanded frontier (BFS: E_s;
                                SSSP: over the near queues, E_s x work inflation) */
     int64_t frontier_total; /* sum of expanded frontier sizes */

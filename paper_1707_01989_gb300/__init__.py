@@ -68,7 +68,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int32), ("barriers", ctypes.c_int32), ("kills", ctypes.c_int32),
                 ("forks", ctypes.c_int32), ("min_active", ctypes.c_int32), ("max_active", ctypes.c_int32),
                 ("initial_active", ctypes.c_int32), ("status", ctypes.c_int32),
-                ("ctas_launched", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("ctas_launched", ctypes.c_int32), ("joined", ctypes.c_int32),
                 ("edges_scanned", ctypes.c_int64), ("frontier_total", ctypes.c_int64),
                 ("vertices_reached", ctypes.c_int64), ("reached_edges", ctypes.c_int64),
                 ("gather_us_max", ctypes.c_double), ("kernel_us", ctypes.c_double)]

@@ -624,7 +624,7 @@ __device__ __forceinline__ uint32_t expand_range_bfs(const Params &p, const Inte
       // the list is full: this iteration goes on (the next one tries again)
     }
     if (more && lane == 0 && c + kIt >= E1 &&
-        !(p.coop && p.kill_mode == KILL_CHUNK && doomed(ld_relaxed64(&p.ctl->kill_target), iv.epoch, id)))
+        !(p.coop && p.kill_mode == KILL_CHUNK && doomed(ld_relaxed64(&p.ctl->kill_target), iv.epoch, id, iv.M)))
       jn = GW + atomicAdd(&p.ctl->cursor.v, 1u);
     if (ci < E1) issue_groups<MODE>(p, qo, qs, qv, F, Etot, ci, E1, w, wb, pf, sn, lane, lm_le);
     else cp_async_commit();
@@ -702,7 +702,7 @@ __device__ __forceinline__ uint32_t expand_range(const Params &p, const Interval
   uint32_t jn = kNoChunk;
   for (uint32_t c = c0; c < E1; c += 32u * kUnroll, ci += 32u * kUnroll) {
     if (more && lane == 0 && c + 32u * kUnroll >= E1 &&
-        !(p.coop && p.kill_mode == KILL_CHUNK && doomed(ld_relaxed64(&p.ctl->kill_target), iv.epoch, id)))
+        !(p.coop && p.kill_mode == KILL_CHUNK && doomed(ld_relaxed64(&p.ctl->kill_target), iv.epoch, id, iv.M)))
       jn = GW + atomicAdd(&p.ctl->cursor.v, 1u);
     if (ci < E1) issue_groups<MODE>(p, qo, qs, qv, F, Etot, ci, E1, w, wb, pf, sn, lane, lm_le);
     else cp_async_commit();
@@ -780,10 +780,6 @@ __device__ __forceinline__ uint32_t expand_range(const Params &p, const Interval
   return __shfl_sync(kFull, jn, 0);
 }
 
-__device__ __forceinline__ uint32_t round_units(uint32_t rem, uint32_t GW, uint32_t cap) {
-  return min(cap, max(1u, (rem + 2u * GW - 1u) / (2u * GW)));
-}
-
 __device__ __forceinline__ void sched_init(ChunkSched &s, uint32_t E, uint32_t GW, uint32_t cap) {
   const bool small = E <= GW * 32u;
   const uint32_t shift = small ? 5u : kIndexShift;
@@ -853,7 +849,8 @@ __device__ void expand(const Params &p, const Interval &iv, int32_t id, WarpStag
   bool bad = false, ovf = false;
   const uint32_t gw = (uint32_t)id * NW + (threadIdx.x >> 5);
   // BFS continuation interval: the returned ranges [lo, lo + n) of the level, range j for
-  // warp j mod GW; otherwise the chunks of the schedule
+  // warp j mod GW; otherwise the chunks of the schedule (a CTA that joined the interval
+  // after it opened, id >= M, takes its chunks from the cursor only)
   const uint32_t cont = MODE == MODE_BFS ? iv.cont : 0u;
   const uint32_t lo = cont >> 16, n = cont & 0xFFFFu;
   uint32_t j = gw;
@@ -868,8 +865,18 @@ __device__ void expand(const Params &p, const Interval &iv, int32_t id, WarpStag
     }
     return false;
   };
-  bool have = cont ? next_range() : sched_chunk(sc, gw, Etot, GW, c0, c1);
   const bool more = !cont && sc.U > GW * sc.s;  // chunks beyond round 0 are claimed from the cursor
+  bool have;
+  if (cont) {
+    have = next_range();
+  } else if (id >= iv.M) {
+    uint32_t k = kNoChunk;
+    if (more && lane == 0) k = GW + atomicAdd(&p.ctl->cursor.v, 1u);
+    k = __shfl_sync(kFull, k, 0);
+    have = k != kNoChunk && sched_chunk(sc, k, Etot, GW, c0, c1);
+  } else {
+    have = sched_chunk(sc, gw, Etot, GW, c0, c1);
+  }
   while (have) {
     uint32_t k;
     if constexpr (MODE == MODE_SSSP)
@@ -980,10 +987,14 @@ __device__ __forceinline__ void scheduler_warp(const Params &p, const volatile i
 __device__ __forceinline__ void doom_watcher(const Params &p, CtaShared &cs) {
   const volatile Interval *iv = &cs.iv;
   const volatile int32_t *left = &cs.workers_left;
+  const volatile int32_t *idp = &cs.id;
   volatile uint32_t *doom = &cs.doom;
   for (;;) {
+    // the epoch first: a barrier writes the CTA's new id before the new interval
     const uint32_t e = iv->epoch;
-    if (doomed(ld_relaxed64(&p.ctl->kill_target), e, cs.id)) *doom = e;
+    __threadfence_block();
+    const int32_t M = iv->M, id = *idp;
+    if (doomed(ld_relaxed64(&p.ctl->kill_target), e, id, M)) *doom = e;
     if (*left != 0 || ld_relaxed(&p.ctl->done) != 0u || ld_relaxed(&p.ctl->err) != 0u) return;
     __nanosleep(256);
   }
@@ -1141,7 +1152,7 @@ template <int MODE, int NW>
 __device__ __forceinline__ void worker_loop(const Params &p, CtaShared &cs, WarpStage *stages, Landing<MODE> *pfs) {
   WarpStage &stage = stages[threadIdx.x >> 5];
   Landing<MODE> &pf = pfs[threadIdx.x >> 5];
-  for (;;) {
+  for (bool first = true;; first = false) {
     const Interval iv = cs.iv;
     const int32_t id = cs.id;
     if (iv.done) {
@@ -1150,7 +1161,9 @@ __device__ __forceinline__ void worker_loop(const Params &p, CtaShared &cs, Warp
       if (MODE == MODE_SSSP && id < iv.M) copy_dist<NW>(p, id, iv.M);
       return;
     }
-    if (id >= iv.M) return;  // left through offer_kill
+    // left through offer_kill at the barrier (a CTA that has just joined the running
+    // interval has an id >= M there)
+    if (id >= iv.M && !first) return;
     if constexpr (MODE == MODE_PSSSP) {
       topo_interval<NW>(p, iv, id);
     } else if constexpr (MODE == MODE_SSSP) {
@@ -1176,7 +1189,7 @@ __device__ __forceinline__ void traverse_body(const Params &p, bool master, CtaS
       master_enter<MODE>(p, cs);
       active = true;
     } else if (p.coop) {
-      active = join_enter(p, cs);
+      active = join_enter<MODE, NW>(p, cs);
     } else {
       active = plain_enter(p, cs);
     }
@@ -2386,6 +2399,7 @@ coop_status coop_get_stats(coop_ctx *c, coop_stats *s) {
   s->max_active = m->max_active;
   s->initial_active = m->initial_active;
   s->ctas_launched = m->ctas_launched;
+  s->joined = m->joined;
   s->edges_scanned = (int64_t)m->edges_scanned;
   s->frontier_total = (int64_t)m->frontier_total;
   s->vertices_reached = (int64_t)m->reached;
@@ -2802,6 +2816,7 @@ coop_status coop_batch_get_stats(coop_batch *b, coop_stats *per_job) {
     st.max_active = m.max_active;
     st.initial_active = m.initial_active;
     st.ctas_launched = m.ctas_launched;
+    st.joined = m.joined;
     st.edges_scanned = (int64_t)m.edges_scanned;
     st.frontier_total = (int64_t)m.frontier_total;
     st.vertices_reached = (int64_t)m.reached;

@@ -151,10 +151,25 @@ struct alignas(128) Word {
   uint32_t v;
   uint32_t pad[31];
 };
+struct alignas(128) Word64 {
+  unsigned long long v;
+  uint32_t pad[30];
+};
+
+// The barrier's arrival word: epoch << 32 | joined << 16 | arrived.  `arrived` counts the
+// interval's CTAs that have reached the barrier; `joined` the CTAs that joined the interval
+// after it opened (a forked CTA takes part in the running BFS level instead of waiting for
+// the next barrier).  The barrier releases when arrived reaches M + joined, so a join and
+// the last arrival are ordered by the one atomic word: a CTA can join only while someone
+// is still working, and the release then waits for it.
+__host__ __device__ constexpr unsigned long long arrive_word(uint32_t epoch, uint32_t joined, uint32_t arrived) {
+  return ((unsigned long long)epoch << 32) | ((unsigned long long)(joined & 0xFFFFu) << 16) |
+         (unsigned long long)(arrived & 0xFFFFu);
+}
 
 // Control block in device memory (L2-resident), zeroed before every run.
 struct Ctl {
-  Word arrive;        // arrivals at the current barrier
+  Word64 arrive;      // arrivals at the current barrier (arrive_word)
   Word epoch;         // release word: bumped by the releaser
   Word join_ticket;   // registrations of CTAs waiting to be admitted
   Word cursor;        // chunks claimed beyond the first M * NW in the current interval
@@ -185,8 +200,8 @@ struct Ctl {
   unsigned long long reached;                     // reached vertices (V_r)
   uint64_t pad_r[14];
   // releaser-private bookkeeping (serialised by the barrier)
-  alignas(128) uint32_t admitted;
-  uint32_t unused_b;
+  alignas(128) uint32_t admitted;  // forked CTAs admitted at barriers (join tickets)
+  uint32_t joined;                 // forked CTAs that joined a running interval
   int32_t barriers, kills, forks, min_active, max_active, initial_active;
   unsigned long long edges_scanned, frontier_total;
   unsigned long long t_start;  // %globaltimer at the master's entry
@@ -215,7 +230,7 @@ struct alignas(128) Mailbox {
   int32_t active;     // device -> host: active CTAs (M) after the latest resizing barrier
   uint32_t pad1[28];
   int32_t levels, barriers, kills, forks, min_active, max_active, initial_active, status;
-  int32_t ctas_launched, pad2;
+  int32_t ctas_launched, joined;
   unsigned long long edges_scanned, frontier_total;
   unsigned long long reached, reached_edges;
 };
@@ -319,6 +334,11 @@ __device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t *p, uint32_t v) {
   asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
   return old;
 }
+__device__ __forceinline__ uint64_t atom_add_acq_rel64(unsigned long long *p, uint64_t v) {
+  uint64_t old;
+  asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+  return old;
+}
 // mapped pinned host memory: generic addressing, system scope
 __device__ __forceinline__ uint32_t ld_sys(const uint32_t *p) {
   uint32_t v;
@@ -371,9 +391,11 @@ __device__ __forceinline__ Interval read_iv(const Ctl *c) {
 // ---------------------------------------------------------------- host kill target
 constexpr unsigned long long kTargetClosed = 1ull << 31;
 
-// Does the kill target word `kt` make logical id `id` of interval `epoch` leave?
-__device__ __forceinline__ bool doomed(uint64_t kt, uint32_t epoch, int32_t id) {
-  return (uint32_t)(kt >> 32) == epoch && (uint32_t)id >= (uint32_t)(kt & 0x7FFFFFFFull);
+// Does the kill target word `kt` make logical id `id` of interval `epoch` (M CTAs at its
+// opening) leave?  A CTA that joined the interval after it opened (id >= M) is never
+// taken by that interval's target: the target counts the opening CTAs only.
+__device__ __forceinline__ bool doomed(uint64_t kt, uint32_t epoch, int32_t id, int32_t M) {
+  return id < M && (uint32_t)(kt >> 32) == epoch && (uint32_t)id >= (uint32_t)(kt & 0x7FFFFFFFull);
 }
 
 // ---------------------------------------------------------------- errors / stats
@@ -397,6 +419,7 @@ __device__ __forceinline__ void publish_stats(const Params &p, int status) {
   st_sys((uint32_t *)&m->initial_active, (uint32_t)c->initial_active);
   st_sys((uint32_t *)&m->status, (uint32_t)status);
   st_sys((uint32_t *)&m->ctas_launched, ld_relaxed(&c->launched_total));
+  st_sys((uint32_t *)&m->joined, c->joined);
   st_sys64(&m->edges_scanned, c->edges_scanned);
   st_sys64(&m->reached, ld_relaxed64(&c->reached));
   st_sys64(&m->reached_edges, ld_relaxed64(&c->reached_edges));
@@ -414,15 +437,16 @@ __device__ __forceinline__ uint64_t slot_pack(uint32_t epoch, uint32_t killed, u
 }
 
 // Wait until the epoch word differs from `e` (a release happened): returns 1.  A CTA
-// with logical id `id` (>= 0) that the host's kill target dooms while it waits returns 2
+// with logical id `id` (>= 0) of an interval that opened with M CTAs, which the host's
+// kill target dooms while it waits, returns 2
 // at once (it has arrived already, and the closed target will include it).  0 on error
 // or timeout.
-__device__ __forceinline__ int wait_release(const Params &p, uint32_t e, int32_t id = -1) {
+__device__ __forceinline__ int wait_release(const Params &p, uint32_t e, int32_t id = -1, int32_t M = 0) {
   Ctl *c = p.ctl;
   const uint64_t t0 = gtime();
   for (uint32_t spin = 0;; ++spin) {
     if (ld_acquire(&c->epoch.v) != e) return 1;
-    if (id > 0 && doomed(ld_relaxed64(&c->kill_target), e, id)) return 2;
+    if (id > 0 && doomed(ld_relaxed64(&c->kill_target), e, id, M)) return 2;
     if (ld_relaxed(&c->err) != 0u) return 0;
     if ((spin & 31u) == 31u) {
       if (gtime() - t0 > p.timeout_ns) {
@@ -465,7 +489,7 @@ __device__ __forceinline__ uint32_t precheck_hint(uint32_t edges) { return edges
 // next releaser's loads.
 struct Books {
   int32_t m_after;  // the new interval's M, for the host mailbox
-  uint32_t admitted;
+  uint32_t admitted, joined;
   int32_t barriers, kills, forks, min_active, max_active;
   unsigned long long edges_scanned, frontier_total;
   uint32_t log_n;
@@ -474,8 +498,10 @@ struct Books {
   int32_t status;  // final status when the traversal is over, else 1
 };
 
+// J CTAs joined the interval after it opened (logical ids M .. M + J - 1): they stay,
+// renumbered right after the opening CTAs that stay, and count as admitted here.
 template <int MODE, int NW>
-__device__ __forceinline__ Interval release_step(const Params &p, const Interval cur, Books &bk) {
+__device__ __forceinline__ Interval release_step(const Params &p, const Interval cur, uint32_t J, Books &bk) {
   Ctl *c = p.ctl;
   const int32_t M = cur.M;
   // (5) of the query barrier for the host's requests: close this interval's kill target.
@@ -505,7 +531,7 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
                                                            : c->qctr[out];
   const uint32_t dmin = (MODE == MODE_SSSP && !was_select) ? ld_relaxed(&c->dmin) : 0xFFFFFFFFu;
   const unsigned long long relaxed = (MODE == MODE_PSSSP) ? c->qctr[1] : 0ull;
-  const uint32_t A = c->admitted;
+  const uint32_t A = c->admitted, Jt = c->joined;
   const uint32_t decided = c->host_decided;
   const int32_t barriers = c->barriers + 1, kills0 = c->kills, forks0 = c->forks;
   const int32_t mina = c->min_active, maxa = c->max_active;
@@ -588,18 +614,20 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
   nxt.done = ((count == 0u && !was_select) || err != 0u) ? 1u : 0u;
 
   const int32_t Wmid = M - Mmid;
+  const int32_t Mj = Mmid + (int32_t)J;  // the opening CTAs that stay, then the joiners
   int32_t k = 0, W = 0, spawned = 0;
   if (!nxt.done && p.coop) {
-    // (2) fork: admit CTAs that registered and wait, up to N - Mmid
-    k = (int32_t)min((uint32_t)(p.N - Mmid), R - A);
+    // (2) fork: admit CTAs that registered and wait, up to N - Mmid - J
+    k = (int32_t)min((uint32_t)(p.N - Mj), R - A);
     int32_t Ws = 0;
     if (p.sched_on) {
       // forced schedule: the scheduler grants up to kcap in [0, N-M] new CTAs (spawned
       // now, admitted when they arrive) and accepts W in [0, M-1] offer_kills
       const uint64_t r = mix64(p.sched_seed ^ mix64((uint64_t)barriers));
       const uint64_t r2 = mix64(r);
-      const int32_t kcap = ((uint32_t)(r >> 32) < p.p_fork) ? (int32_t)(r2 % (uint64_t)(p.N - Mmid + 1)) : 0;
-      const int32_t pending = (int32_t)(ld_relaxed(&c->launched_total) - 1u - A);
+      const int32_t kcap = ((uint32_t)(r >> 32) < p.p_fork) ? (int32_t)(r2 % (uint64_t)(p.N - Mj + 1)) : 0;
+      // launched, and neither admitted at an earlier barrier nor joined
+      const int32_t pending = (int32_t)(ld_relaxed(&c->launched_total) - 1u - A - Jt - J);
       const int32_t spawn = kcap - pending;
       if (spawn > 0) {
         atomicAdd(&c->launched_total, (uint32_t)spawn);
@@ -609,12 +637,12 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
       if ((uint32_t)r < p.p_kill) Ws = (int32_t)((r2 >> 32) % (uint64_t)Mmid);
     }
     // (3) query for the forced schedule's kills (never CTA 0)
-    W = min(Ws, Mmid + k - 1);
+    W = min(Ws, Mj + k - 1);
   }
-  const int32_t Mn = Mmid + k - W;
+  const int32_t Mn = Mj + k - W;
   for (int32_t i = 0; i < k; ++i) {
     const uint32_t t = A + (uint32_t)i;
-    const uint32_t idv = (uint32_t)(Mmid + i);
+    const uint32_t idv = (uint32_t)(Mj + i);
     st_relaxed64(&c->slot[t % kMaxCtas], slot_pack(nxt.epoch, idv >= (uint32_t)Mn, idv, t));
   }
   // read by the scheduler warp together with the interval: published with it
@@ -628,11 +656,12 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
 
   bk.m_after = Mn;
   bk.admitted = A + (uint32_t)k;
+  bk.joined = Jt + J;
   bk.barriers = barriers;
   bk.kills = kills0 + Wmid + W;
-  bk.forks = forks0 + k;
+  bk.forks = forks0 + k + (int32_t)J;
   bk.min_active = min(mina, min(Mmid, Mn));
-  bk.max_active = max(maxa, Mn);
+  bk.max_active = max(maxa, max(M + (int32_t)J, Mn));
   // edges and vertices of the frontiers the traversal expands (SSSP: not the pending
   // queues that a select interval splits)
   const bool expands = !nxt.done && !cont && (MODE != MODE_SSSP || !sssp_select(nxt));
@@ -643,8 +672,10 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
   bk.has_kill = Wmid > 0 && log_n < (uint32_t)kLogCap;  // the host kills of the interval
   bk.kill_rec = LogRec{barriers, t_us, M, 0, Wmid, Mmid, 0, (int32_t)edges};
   const uint32_t ln = log_n + (bk.has_kill ? 1u : 0u);
-  bk.has_rec = ln < (uint32_t)kLogCap && (ln < (uint32_t)kLogCap / 2u || (k | W | spawned) != 0);
-  bk.rec = LogRec{barriers, t_us, Mmid, k, W, Mn, spawned, (int32_t)edges};
+  // the joiners are logged as admitted at this barrier (the trace's fork count)
+  const int32_t kj = k + (int32_t)J;
+  bk.has_rec = ln < (uint32_t)kLogCap && (ln < (uint32_t)kLogCap / 2u || (kj | W | spawned) != 0);
+  bk.rec = LogRec{barriers, t_us, Mmid, kj, W, Mn, spawned, (int32_t)edges};
   bk.log_n = log_n;
   bk.status = nxt.done ? (err ? (int)err : (ld_relaxed(&c->ovf) ? (int)ERR_OVERFLOW : 0)) : 1;
   return nxt;
@@ -654,6 +685,7 @@ __device__ __forceinline__ Interval release_step(const Params &p, const Interval
 __device__ __forceinline__ void release_books(const Params &p, const Books &bk) {
   Ctl *c = p.ctl;
   c->admitted = bk.admitted;
+  c->joined = bk.joined;
   c->barriers = bk.barriers;
   c->kills = bk.kills;
   c->forks = bk.forks;
@@ -698,23 +730,38 @@ __device__ __forceinline__ bool resizing_barrier(const Params &p, CtaShared &cs)
         lv = prev;
       }
     }
-    const uint32_t old = atom_add_acq_rel(&c->arrive.v, 1u);
-    bool ok = true;
-    if (old == (uint32_t)(cur.M - 1) + p.extra_wait) {
+    const uint64_t old = atom_add_acq_rel64(&c->arrive.v, 1ull);
+    const uint32_t J = (uint32_t)(old >> 16) & 0xFFFFu;  // final: no CTA joins once all have arrived
+    bool ok = true, next = false;
+    Interval nxt;
+    if (((uint32_t)old & 0xFFFFu) == (uint32_t)(cur.M - 1) + J + p.extra_wait) {
       Books bk;
-      const Interval nxt = release_step<MODE, NW>(p, cur, bk);
-      st_relaxed(&c->arrive.v, 0u);
+      nxt = release_step<MODE, NW>(p, cur, J, bk);
+      st_relaxed64(&c->arrive.v, arrive_word(cur.epoch + 1u, 0u, 0u));
       st_release(&c->epoch.v, cur.epoch + 1u);
       release_books(p, bk);
-      cs.iv = nxt;
+      next = true;
     } else if (!leave) {
-      const int w = wait_release(p, cur.epoch, (p.coop && p.kill_mode != KILL_SIMPLE) ? cs.id : -1);
+      const int w = wait_release(p, cur.epoch, (p.coop && p.kill_mode != KILL_SIMPLE) ? cs.id : -1, cur.M);
       ok = w != 0;
-      if (w == 1) cs.iv = read_iv(c);
+      if (w == 1) {
+        nxt = read_iv(c);
+        next = true;
+      }
       if (w == 2) leave = true;
     }
-    // a CTA that waited may still be inside the target as it was closed by the release
-    if (ok && !leave && p.coop && cs.id >= (int32_t)cs.iv.doom) leave = true;  // cs.iv is the new interval here
+    if (next) {
+      int32_t id = cs.id;
+      if (id >= cur.M) {
+        id = (int32_t)nxt.doom + (id - cur.M);  // joined during cur: after the opening CTAs that stay
+      } else if (p.coop && id >= (int32_t)nxt.doom) {
+        leave = true;  // a CTA that waited may still be inside the target as the release closed it
+      }
+      // the id before the interval: the doom watcher reads the interval's epoch first
+      *(volatile int32_t *)&cs.id = id;
+      __threadfence_block();
+      cs.iv = nxt;
+    }
     if (leave) atomicAdd(&c->surrendered, 1u);
     cs.ok = ok ? 1 : 0;
     cs.leave = leave ? 1 : 0;
@@ -724,11 +771,60 @@ __device__ __forceinline__ bool resizing_barrier(const Params &p, CtaShared &cs)
 }
 
 // ---------------------------------------------------------------- entry
-// A CTA that is not the master registers and waits for a release that admits it
-// (request_fork seen from the forked side).  Returns false if it should leave.
+// Units per chunk in a round of the guided chunk schedule that has `rem` units left to
+// deal over GW warps: half the remainder spread evenly, 1 .. cap.
+__host__ __device__ __forceinline__ uint32_t round_units(uint32_t rem, uint32_t GW, uint32_t cap) {
+  return min(cap, max(1u, (rem + 2u * GW - 1u) / (2u * GW)));
+}
+
+// Can a CTA join interval iv while it runs?  A BFS level (not a continuation of one)
+// whose chunk schedule deals chunks beyond its first round -- claimed from the shared
+// cursor by whichever warp is free, so a CTA that arrives late can take some.
+template <int MODE, int NW>
+__device__ __forceinline__ bool joinable(const Params &p, const Interval &iv) {
+  if (MODE != MODE_BFS || !p.coop || p.kill_mode == KILL_SIMPLE || p.extra_wait != 0u) return false;
+  if (iv.done || iv.cont != 0u || iv.M < 1) return false;
+  const uint32_t GW = (uint32_t)iv.M * NW;
+  if (iv.edges <= GW * 32u) return false;  // one 32-edge chunk per warp, nothing left over
+  const uint32_t U = (iv.edges + kIndexEdges - 1u) >> kIndexShift;
+  return U > GW * round_units(U, GW, kChunkUnitsMax);
+}
+
+// A forked CTA joins the running interval if it can (joinable; fewer than N CTAs in it;
+// not all of its CTAs at the barrier yet): one CAS on the arrival word adds it to the
+// barrier's count, and its logical id for the interval is M + (joiners before it).
+// False if it cannot; it then registers for admission at the next barrier.
+template <int MODE, int NW>
+__device__ __forceinline__ bool join_running(const Params &p, CtaShared &cs) {
+  Ctl *c = p.ctl;
+  const uint32_t e = ld_acquire(&c->epoch.v);
+  if (e == 0u) return false;  // the master has not opened the first interval
+  const Interval iv = read_iv(c);
+  if (iv.epoch != e || !joinable<MODE, NW>(p, iv)) return false;
+  unsigned long long w = ld_relaxed64(&c->arrive.v);
+  for (int tries = 0; tries < 64; ++tries) {
+    const uint32_t J = (uint32_t)(w >> 16) & 0xFFFFu, a = (uint32_t)w & 0xFFFFu;
+    // another epoch (released since), everyone arrived (releasing), or full
+    if ((uint32_t)(w >> 32) != e || a >= (uint32_t)iv.M + J || (int32_t)((uint32_t)iv.M + J) >= p.N) return false;
+    const unsigned long long prev = atomicCAS(&c->arrive.v, w, w + (1ull << 16));
+    if (prev == w) {
+      cs.iv = iv;
+      cs.id = iv.M + (int32_t)J;
+      return true;
+    }
+    w = prev;
+  }
+  return false;
+}
+
+// A CTA that is not the master joins the running interval (join_running), or registers
+// and waits for a release that admits it (request_fork seen from the forked side).
+// Returns false if it should leave.
+template <int MODE, int NW>
 __device__ __forceinline__ bool join_enter(const Params &p, CtaShared &cs) {
   Ctl *c = p.ctl;
   if (ld_relaxed(&c->run) != p.run || ld_relaxed(&c->done) != 0u || ld_relaxed(&c->err) != 0u) return false;
+  if (join_running<MODE, NW>(p, cs)) return true;
   const uint32_t t = atomicAdd(&c->join_ticket.v, 1u);
   const uint64_t t0 = gtime();
   uint64_t s = 0;
@@ -853,6 +949,7 @@ __device__ __forceinline__ void master_enter(const Params &p, CtaShared &cs) {
     const uint32_t e = ld_relaxed(&c->err);
     publish_stats(p, (int)e);
   }
+  c->arrive.v = arrive_word(1u, 0u, 0u);
   st_release(&c->epoch.v, 1u);
   if (p.coop) st_sys((uint32_t *)&p.mbox->active, (uint32_t)iv.M);
   cs.iv = iv;

@@ -489,3 +489,40 @@ def test_chunks_handed_back_mid_level_are_expanded_in_a_continuation(ctx):
     assert bad == 0, (bad, runs)
     assert all(got == n for n, got in grants) and len(grants) > 20
     assert cont_runs > 0, "no traversal expanded a returned range"
+
+
+@pytest.mark.slow
+def test_forked_ctas_join_a_running_level(ctx):
+    """request_fork (Sec. 3.1) while a wide BFS level runs: the host lends half the CTAs
+    before each R-MAT 22 traversal (which then starts on the other half) and gives them
+    back while it runs.  The forked CTAs join the level in flight -- one CAS on the
+    barrier's arrival word, then chunks from the level's shared cursor -- instead of
+    waiting for its end.  Every traversal's levels equal the oracle's, every resize log
+    is a legal Fork/Kill sequence, and some traversals record mid-level joiners."""
+    import torch
+    g = gg.rmat(22, 16, seed=22)
+    src = gg.max_out_degree_vertex(g)
+    dg = DevGraph(g)
+    ref = torch.from_numpy(oracle.bfs(g, src)).to(dg.device)
+    lv = dg.empty()
+    N = coop.coop_query(ctx)["max_ctas"]
+    half = N // 2
+    s = torch.cuda.Stream(device=dg.device)
+    runs_joined, joined_total = 0, 0
+    for i in range(24):
+        got = coop.coop_request_resources(ctx, half, timeout_us=2_000_000)  # idle: granted at once
+        assert got == half
+        coop.coop_bfs(ctx, dg.csr, src, lv, stream=s)  # on N - half CTAs, asynchronous
+        time.sleep(0.00005 * (i % 6))
+        coop.coop_release(ctx, got)
+        s.synchronize()
+        st = coop.coop_get_stats(ctx)
+        assert st.status == coop.COOP_OK, st.status
+        assert torch.equal(lv, ref), f"run {i}: levels differ from the oracle"
+        assert st.initial_active == N - half
+        assert 0 <= st.joined <= st.forks <= half, (st.joined, st.forks)
+        _replay(ctx, st)
+        runs_joined += st.joined > 0
+        joined_total += st.joined
+    assert coop.coop_sync(ctx) == coop.COOP_OK
+    assert runs_joined > 0, "no forked CTA joined a running level"
