@@ -468,7 +468,7 @@ class gil_handover:
         sys.setswitchinterval(self.old)
 
 
-def corunner(coop, ctx, dev, csr, src, lv, stream, period_s=1.0 / 60.0, duration_s=3.0, work=None):
+def corunner(coop, ctx, dev, csr, src, lv, stream, period_s=1.0 / 60.0, duration_s=6.0, work=None, n_solo=360):
     """Cooperative multitasking: a periodic fp32 saxpy over 64 MB (x and y, 16.7 ms period)
     that claims half the SMs from back-to-back R-MAT 22 BFS traversals.
 
@@ -497,7 +497,7 @@ def corunner(coop, ctx, dev, csr, src, lv, stream, period_s=1.0 / 60.0, duration
         coop.coop_release(ctx, got)
         return (t2 - t0) * 1e3, (t1 - t0) * 1e3
 
-    solo = [job()[0] for _ in range(40)]
+    solo = [job()[0] for _ in range(n_solo)]  # as many as the co-run's jobs: the same p99 estimator
     # traversal throughput alone
     coop.coop_bfs(ctx, csr, src, lv, stream=stream)
     stream.synchronize()
@@ -524,7 +524,7 @@ def corunner(coop, ctx, dev, csr, src, lv, stream, period_s=1.0 / 60.0, duration
     th = threading.Thread(target=ticker)
     coop.coop_get_request_log(ctx, clear=True)
     with gil_handover():
-        t0 = time.perf_counter()
+        t0, c0 = time.perf_counter(), time.process_time()
         th.start()
         n_co = 0
         while time.perf_counter() - t0 < duration_s:
@@ -534,10 +534,11 @@ def corunner(coop, ctx, dev, csr, src, lv, stream, period_s=1.0 / 60.0, duration
         per_co = (time.perf_counter() - t0) / n_co
         stop.set()
         th.join()
+        cores = (time.process_time() - c0) / (time.perf_counter() - t0)
     coop.coop_sync(ctx)
     reqs = coop.coop_get_request_log(ctx, clear=True)
     slowest = sorted(reqs, key=lambda r: -r["gather_us"])[:3]
-    dev_gather = [r["gather_us"] / 1e3 for r in reqs if r["active_at_post"] > 0]
+    dev_gather = [r["gather_us"] / 1e3 for r in reqs]
     run = [l - g for l, g in zip(lat, gat)]
 
     def pct(v, q):
@@ -554,6 +555,7 @@ def corunner(coop, ctx, dev, csr, src, lv, stream, period_s=1.0 / 60.0, duration
             "gather_ms_lib_p50": pct(dev_gather or [0.0], 0.5), "gather_ms_lib_p99": pct(dev_gather or [0.0], 0.99),
             "run_ms_p50": pct(run, 0.5), "run_ms_p99": pct(run, 0.99),
             "deadline_ms": 2.0, "deadline_met_frac": round(sum(l <= 2.0 for l in lat) / max(1, len(lat)), 4),
+            "host_cores_busy": round(cores, 2),  # this process's CPU time / wall time while co-running
             "traversal_ms_alone": round(per_alone * 1e3, 4), "traversal_ms_corun": round(per_co * 1e3, 4),
             "coop_slowdown": round(per_co / per_alone, 4),
             # per-request records of the three slowest gathers: M when posted and granted
@@ -1201,14 +1203,14 @@ def serving(coop, dev, n_graphs=32, rate=200.0, duration_s=3.0, slots=4, budget=
             "all_ok": all(r.status == 0 for r in done)}
 
 
-EXTRAS = ("sssp_rmat20", "bfs_rmat22", "grid_bfs", "preemption", "gather_by_kill_mode", "occupancy_trace",
+EXTRAS = ("sssp_rmat20", "bfs_rmat22", "corunner", "grid_bfs", "preemption", "gather_by_kill_mode", "occupancy_trace",
           "topology_driven_sssp", "octree", "batched", "serving", "barrier_us")
 
 
 def selected_extras(spec: str):
     """The secondary figures named by --extras, in their fixed order ("all" = every one)."""
-    if spec.strip() == "all":
-        return EXTRAS
+    if spec.strip() == "all":  # the co-runner alone is part of bfs_rmat22 already
+        return tuple(x for x in EXTRAS if x != "corunner")
     names = [x.strip() for x in spec.split(",") if x.strip()]
     bad = [x for x in names if x not in EXTRAS]
     if bad:
@@ -1270,8 +1272,7 @@ def secondary(coop, ctx, dev, stream, flush, args, head):
         m["parity_vs_oracle"] = m.pop("parity_last_step")
         return m
 
-    def rmat22():
-        # BFS on R-MAT scale 22: the non-cooperative baseline, schedules and the co-runner
+    def rmat22_graph():
         ref = None
         if args.workload == "rmat22-bfs":
             g, src, ro, col, csr, ref = head["_graph"]
@@ -1283,6 +1284,25 @@ def secondary(coop, ctx, dev, stream, flush, args, head):
             csr = coop.make_csr(ro, col)
         if ref is None:
             ref = oracle_run(g, None, src, "bfs")
+        return g, src, csr, ref
+
+    def corunner_only():
+        # the co-runner beside back-to-back R-MAT 22 BFS traversals, alone
+        g, src, csr, ref = rmat22_graph()
+        lv = torch.empty(g.num_vertices, dtype=torch.int32, device=dev)
+        coop.coop_bfs(ctx, csr, src, lv, stream=stream)
+        stream.synchronize()
+        vr, es = reached_work(g, ref >= 0)
+        B = 4 * g.num_vertices + 20 * vr + 8 * es
+        with ClockSampler(dev.index or 0) as ck:
+            res = corunner(coop, ctx, dev, csr, src, lv, stream, work=(es, B, hbm))
+        res["clocks"] = ck.summary()
+        res["bit_exact"] = bool(np.array_equal(lv.cpu().numpy(), ref))
+        return res
+
+    def rmat22():
+        # BFS on R-MAT scale 22: the non-cooperative baseline, schedules and the co-runner
+        g, src, csr, ref = rmat22_graph()
         lv = torch.empty(g.num_vertices, dtype=torch.int32, device=dev)
         f = lambda: coop.coop_bfs(ctx, csr, src, lv, stream=stream)
         for _ in range(3):
@@ -1352,6 +1372,7 @@ def secondary(coop, ctx, dev, stream, flush, args, head):
     parts = {
         "sssp_rmat20": lambda: guarded("sssp_rmat20", sssp_rmat20),
         "bfs_rmat22": lambda: guarded(None, rmat22, "bfs_rmat22"),
+        "corunner": lambda: guarded("corunner", corunner_only),
         "grid_bfs": lambda: guarded("grid_bfs", grid),
         "preemption": lambda: guarded("preemption", lambda: preemption(coop, ctx, dev, stream)),
         "gather_by_kill_mode": lambda: guarded("gather_by_kill_mode", lambda: gather_by_kill_mode(coop, ctx, dev, stream)),

@@ -182,12 +182,14 @@ coop_status coop_get_resize_log(coop_ctx *ctx, int32_t *out, int cap, int *n);
 
 /*
  * Record of the scheduler's requests (Sec. 4.2: the gather time of a request for
- * workgroups): one record per coop_request_resources call, six doubles each:
+ * workgroups): one record per coop_request_resources call, eight doubles each:
  * {microseconds from coop_init to the request, CTAs asked for, active CTAs M when the
  * request was posted, M when it was granted, gather microseconds (request to grant),
- * CTAs granted}.  M is the count the device published at its latest resizing barrier
- * (0 for a request granted at once, with no traversal in flight).  Writes the latest
- * min(cap, available) records, oldest first, to out (host memory, 6*cap doubles) and
+ * CTAs granted, microseconds spent waiting for the context's lock, microseconds from
+ * the call to the request's posting (the lock wait included)}.  M is the count the
+ * device published at its latest resizing barrier (0 for a request granted at once,
+ * with no traversal in flight).  Writes the latest min(cap, available) records, oldest
+ * first, to out (host memory, 8*cap doubles) and
  * the number written to *n; with clear != 0 the context's record is emptied after the
  * copy.  A context keeps its latest 4096 records.  Host-side only: it never waits for
  * the GPU.

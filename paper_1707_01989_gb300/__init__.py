@@ -353,16 +353,18 @@ def coop_get_resize_log(ctx, cap: int = 4096):
     return [tuple(buf[8 * i: 8 * i + 8]) for i in range(n.value)]
 
 
-REQUEST_FIELDS = ("t_us", "n_ctas", "active_at_post", "active_at_grant", "gather_us", "granted")
+REQUEST_FIELDS = ("t_us", "n_ctas", "active_at_post", "active_at_grant", "gather_us", "granted", "lock_us",
+                  "post_us")
 
 
 def coop_get_request_log(ctx, cap: int = 4096, clear: bool = True):
     """The context's coop_request_resources records, oldest first, as dicts of REQUEST_FIELDS."""
-    buf = (ctypes.c_double * (6 * cap))()
+    k = len(REQUEST_FIELDS)
+    buf = (ctypes.c_double * (k * cap))()
     n = ctypes.c_int(0)
     _check(load_library().coop_get_request_log(_h(ctx), buf, cap, ctypes.byref(n), 1 if clear else 0),
            "coop_get_request_log")
-    return [dict(zip(REQUEST_FIELDS, buf[6 * i: 6 * i + 6])) for i in range(n.value)]
+    return [dict(zip(REQUEST_FIELDS, buf[k * i: k * i + k])) for i in range(n.value)]
 
 
 def coop_set_schedule(ctx, seed: int, p_kill: float, p_fork: float) -> None:

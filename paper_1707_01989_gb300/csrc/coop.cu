@@ -430,12 +430,32 @@ __device__ __forceinline__ void select_interval(const Params &p, const Interval 
     cs.split[1] = 0xFFFFFFFFu;
     cs.take[0][0] = cs.take[0][1] = cs.take[1][0] = cs.take[1][1] = 0ull;
   }
+  const uint32_t step = GW * 32u;
+  // the entries of the first batch (kSelectBatch stripes per warp) and their current
+  // distances, loaded once: they are the histogram's sample and the first batch's input
+  uint32_t v[kSelectBatch], rs[kSelectBatch], deg[kSelectBatch], dd[kSelectBatch];
+  const auto load_batch = [&](uint32_t i0) {
+#pragma unroll
+    for (int k = 0; k < kSelectBatch; ++k) {
+      const uint32_t i = i0 + (uint32_t)k * step + lane;
+      v[k] = 0u;
+      rs[k] = 0u;
+      deg[k] = 0u;
+      if (i < F) {
+        v[k] = qv[i];
+        rs[k] = qs[i];
+        deg[k] = (i + 1u < F ? qo[i + 1u] : Etot) - qo[i];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kSelectBatch; ++k)
+      dd[k] = i0 + (uint32_t)k * step + lane < F ? (uint32_t)(__ldcg(p.ds + v[k]) >> 32) : 0u;
+  };
+  load_batch(first);
   workers_sync<NW>();
-  if (first + lane < F) {
-    const uint32_t i = first + lane;
-    const uint32_t deg = (i + 1u < F ? qo[i + 1u] : Etot) - qo[i];
-    atomicAdd(&hs[dist_bucket((uint32_t)(__ldcg(p.ds + qv[i]) >> 32), iv.base)], deg);
-  }
+#pragma unroll
+  for (int k = 0; k < kSelectBatch; ++k)
+    if (first + (uint32_t)k * step + lane < F) atomicAdd(&hs[dist_bucket(dd[k], iv.base)], deg[k]);
   workers_sync<NW>();
   if (warp == 0) {
     // the first bucket with cum * Etot >= B * total: lane l sums segment l (32 buckets),
@@ -471,30 +491,17 @@ __device__ __forceinline__ void select_interval(const Params &p, const Interval 
   const uint32_t bstar = cs.split[0];
   const uint32_t tag = sssp_tag(iv);
   uint32_t dmin = 0xFFFFFFFFu;
-  const uint32_t step = GW * 32u;
   // batches: the same count for every warp of the CTA (they meet at two CTA syncs each)
   const uint32_t nb = (F + kSelectBatch * step - 1u) / (kSelectBatch * step);
   for (uint32_t bi = 0, i0 = first; bi < nb; ++bi, i0 += kSelectBatch * step) {
     unsigned long long *take = cs.take[bi & 1u];
-    uint32_t v[kSelectBatch], rs[kSelectBatch], deg[kSelectBatch];
     bool near[kSelectBatch], far[kSelectBatch];
-#pragma unroll
-    for (int k = 0; k < kSelectBatch; ++k) {
-      const uint32_t i = i0 + (uint32_t)k * step + lane;
-      v[k] = 0u;
-      rs[k] = 0u;
-      deg[k] = 0u;
-      if (i < F) {
-        v[k] = qv[i];
-        rs[k] = qs[i];
-        deg[k] = (i + 1u < F ? qo[i + 1u] : Etot) - qo[i];
-      }
-    }
+    if (bi > 0u) load_batch(i0);
     uint32_t nN = 0u, nF = 0u, eN = 0u, eF = 0u;
 #pragma unroll
     for (int k = 0; k < kSelectBatch; ++k) {
       const bool valid = i0 + (uint32_t)k * step + lane < F;
-      const uint32_t d = valid ? (uint32_t)(__ldcg(p.ds + v[k]) >> 32) : 0u;
+      const uint32_t d = dd[k];
       near[k] = valid && dist_bucket(d, iv.base) <= bstar;
       far[k] = valid && !near[k];
       if (near[k]) dmin = min(dmin, d);
@@ -1862,6 +1869,8 @@ const void *octree_fn(int nw) {
 
 // ===================================================================== host side
 
+constexpr int kReqFields = 8;  // doubles per coop_request_resources record
+
 struct coop_ctx {
   int device = 0;
   int nw = kDefaultWorkerWarps;  // worker warps per traversal CTA
@@ -1887,6 +1896,7 @@ struct coop_ctx {
   std::mutex launch_mu;  // serialises traversal launches
   uint32_t run = 0;
   bool launched = false;
+  bool launching = false;  // a traversal's parameters are fixed and its launch is under way
   Params cur{};
   int cur_mode = MODE_BFS;
   uint32_t kill_req = 0, served = 0, returned = 0, fork_req = 0;
@@ -1895,9 +1905,10 @@ struct coop_ctx {
   double p_kill = 0.0, p_fork = 0.0;
   double gather_us_max = 0.0;
   // coop_request_resources records: {posted (us since coop_init), CTAs asked for, M when
-  // posted, M when granted, gather us, CTAs granted}; the latest kReqLog
+  // posted, M when granted, gather us, CTAs granted, us waiting for the context lock, us
+  // posting}; the latest kReqLog
   std::chrono::steady_clock::time_point t_init = std::chrono::steady_clock::now();
-  std::deque<std::array<double, 6>> req_log;
+  std::deque<std::array<double, kReqFields>> req_log;
 };
 
 namespace {
@@ -1940,14 +1951,25 @@ bool set_traverse_attrs(const void *k, int smem) {
                       "set traversal carveout");
 }
 
-bool running(coop_ctx *c) { return c->launched && cudaEventQuery(c->ev_done) == cudaErrorNotReady; }
+bool running(coop_ctx *c) {
+  return c->launching || (c->launched && cudaEventQuery(c->ev_done) == cudaErrorNotReady);
+}
+
+// The latest traversal has made its final release (the device wrote its run id after
+// the stats): its CTAs are leaving, so a request need not wait for its completion event.
+bool finished_locked(coop_ctx *c) {
+  return c->launched && !c->launching && load_acquire(&c->mbox->run_done) == c->cur.run;
+}
+
+// A traversal holds CTAs that a request must wait for.
+bool busy_locked(coop_ctx *c) { return !finished_locked(c) && running(c); }
 
 // Fold the CTAs the device has surrendered into the host's books (always), and once no
-// traversal is in flight grant every still-outstanding request at once.
+// traversal holds CTAs grant every still-outstanding request at once.
 void finalize_locked(coop_ctx *c) {
   const uint32_t f = load_acquire(&c->mbox->freed);
   if ((int32_t)(f - c->served) > 0) c->served = f;
-  if (running(c)) return;
+  if (busy_locked(c)) return;
   (void)cudaGetLastError();
   if ((int32_t)(c->kill_req - c->served) > 0) c->served = c->kill_req;  // idle grant
   store_release(&c->mbox->freed, c->served);
@@ -1955,32 +1977,37 @@ void finalize_locked(coop_ctx *c) {
 
 // The two halves of coop_request_resources.  post_kill raises the cumulative request by
 // n (offer_kill asked of the running kernel) and returns the count the device's `freed`
-// must reach; with no traversal in flight the request is granted at once (*granted).
-coop_status post_kill(coop_ctx *c, int n, uint32_t *target, bool *granted) {
+// must reach and the id of the run asked (*run); with no traversal holding CTAs the
+// request is granted at once (*granted).
+coop_status post_kill(coop_ctx *c, int n, uint32_t *target, bool *granted, double *lock_us, uint32_t *run) {
+  const auto t0 = std::chrono::steady_clock::now();
   std::lock_guard<std::mutex> lk(c->mu);
+  *lock_us = std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count();
   finalize_locked(c);
   const int outstanding = (int)(c->kill_req - c->returned);
   if (outstanding + n > c->N - 1) return COOP_EINVAL;
   c->kill_req += (uint32_t)n;
   *target = c->kill_req;
   store_release(&c->mbox->kill_req, c->kill_req);
-  *granted = !running(c);
+  *run = c->cur.run;
+  *granted = !busy_locked(c);
   if (*granted) finalize_locked(c);
   return COOP_OK;
 }
 
 // Waits until the device has freed the CTAs of a posted request (or the traversal ended,
-// which grants the rest), or until `deadline`; *got = the request's CTAs freed so far.
-coop_status wait_kill(coop_ctx *c, uint32_t target, int n, bool bounded,
+// which grants the rest: seen first as the run's id in the mailbox, then as its
+// completion), or until `deadline`; *got = the request's CTAs freed so far.
+coop_status wait_kill(coop_ctx *c, uint32_t target, int n, uint32_t run, bool bounded,
                       std::chrono::steady_clock::time_point deadline, int *got) {
   const auto t0 = std::chrono::steady_clock::now();
   for (uint32_t spin = 0;; ++spin) {
     const uint32_t f = load_acquire(&c->mbox->freed);
     *got = std::max(0, std::min(n, (int)(f - (target - (uint32_t)n))));
     if ((int32_t)(f - target) >= 0) break;
-    if ((spin & 63u) == 0u) {
+    if ((spin & 63u) == 0u || load_acquire(&c->mbox->run_done) == run) {
       std::lock_guard<std::mutex> lk(c->mu);
-      if (!running(c)) {
+      if (!busy_locked(c)) {
         finalize_locked(c);
         break;
       }
@@ -2072,6 +2099,8 @@ coop_status launch_run(coop_ctx *c, const coop_csr *g, const uint32_t *w, int32_
   // state lock, so the scheduler's calls from other threads never queue behind a GPU wait.
   std::lock_guard<std::mutex> launch_lk(c->launch_mu);
   if (c->launched) cudaEventSynchronize(c->ev_done);
+  Params p{};
+  int launched = 0;
   {
     std::lock_guard<std::mutex> lk(c->mu);
     finalize_locked(c);
@@ -2079,8 +2108,7 @@ coop_status launch_run(coop_ctx *c, const coop_csr *g, const uint32_t *w, int32_
     coop_status st = ensure_scratch(c, std::max<int64_t>(V, 1), g ? g->num_edges : 0);
     if (st != COOP_OK) return st;
     const int held = (int)(c->served - c->returned);
-    const int launched = coop ? std::max(1, c->N - held) : c->N;
-    Params p{};
+    launched = coop ? std::max(1, c->N - held) : c->N;
     if (g) {
       p.row_off = g->row_off;
       p.col = g->col;
@@ -2125,18 +2153,26 @@ coop_status launch_run(coop_ctx *c, const coop_csr *g, const uint32_t *w, int32_
     store_release(&c->mbox->freed, c->served);
     store_release(&c->mbox->kill_req, c->kill_req);
     store_release(&c->mbox->fork_req, c->fork_req);
-
-    coop_init_kernel<MODE><<<c->sm_count * 4, 512, 0, stream>>>(p);
-    if (c->timing) cudaEventRecord(c->ev_t0, stream);
-    launch_traverse<MODE>(c->nw, launched, p, 0, stream);
-    if (c->timing) cudaEventRecord(c->ev_t1, stream);
-    cudaEventRecord(c->ev_done, stream);
-    if (cuda_failed(cudaGetLastError(), "traversal launch")) return COOP_ECUDA;
+    // From here on a request or a release is the new traversal's (kill_base and fork_base
+    // are fixed above); the launch calls run without the state lock, so that a request
+    // never waits behind them.
+    c->launching = true;
     c->cur = p;
     c->cur_mode = MODE;
-    c->launched = true;
     c->gather_us_max = 0.0;
   }
+  coop_init_kernel<MODE><<<c->sm_count * 4, 512, 0, stream>>>(p);
+  if (c->timing) cudaEventRecord(c->ev_t0, stream);
+  launch_traverse<MODE>(c->nw, launched, p, 0, stream);
+  if (c->timing) cudaEventRecord(c->ev_t1, stream);
+  cudaEventRecord(c->ev_done, stream);
+  const bool failed = cuda_failed(cudaGetLastError(), "traversal launch");
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->launching = false;
+    c->launched = !failed;
+  }
+  if (failed) return COOP_ECUDA;
   if (stats) {
     if (cudaEventSynchronize(c->ev_done) != cudaSuccess) return COOP_ECUDA;
     return coop_get_stats(c, stats);
@@ -2326,13 +2362,16 @@ coop_status coop_request_resources(coop_ctx *c, int n, int timeout_us, int *n_fr
   bool granted = false;
   const auto t0 = std::chrono::steady_clock::now();
   const int m_post = __atomic_load_n(&c->mbox->active, __ATOMIC_ACQUIRE);
-  const coop_status st = post_kill(c, n, &target, &granted);
+  double lock_us = 0.0;
+  uint32_t run = 0;
+  const coop_status st = post_kill(c, n, &target, &granted, &lock_us, &run);
   if (st != COOP_OK) return st;
+  const double post_us = std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count();
   int got = n;
   coop_status w = COOP_OK;
   if (!granted) {
     const auto deadline = t0 + std::chrono::microseconds(std::max(0, timeout_us));
-    w = wait_kill(c, target, n, timeout_us > 0, deadline, &got);
+    w = wait_kill(c, target, n, run, timeout_us > 0, deadline, &got);
   }
   if (n_freed) *n_freed = got;
   const auto t1 = std::chrono::steady_clock::now();
@@ -2340,7 +2379,7 @@ coop_status coop_request_resources(coop_ctx *c, int n, int timeout_us, int *n_fr
   std::lock_guard<std::mutex> lk(c->mu);
   c->req_log.push_back({std::chrono::duration<double, std::micro>(t0 - c->t_init).count(), (double)n,
                         granted ? 0.0 : (double)m_post, granted ? 0.0 : (double)m_grant,
-                        std::chrono::duration<double, std::micro>(t1 - t0).count(), (double)got});
+                        std::chrono::duration<double, std::micro>(t1 - t0).count(), (double)got, lock_us, post_us});
   if (c->req_log.size() > kReqLog) c->req_log.pop_front();
   return w;
 }
@@ -2351,7 +2390,7 @@ coop_status coop_get_request_log(coop_ctx *c, double *out, int cap, int *n, int 
   const int take = std::min<int>(cap, (int)c->req_log.size());
   const size_t first = c->req_log.size() - (size_t)take;  // the latest `take` records
   for (int i = 0; i < take; ++i)
-    for (int j = 0; j < 6; ++j) out[6 * (size_t)i + j] = c->req_log[first + (size_t)i][j];
+    for (int j = 0; j < kReqFields; ++j) out[kReqFields * (size_t)i + j] = c->req_log[first + (size_t)i][j];
   *n = take;
   if (clear) c->req_log.clear();
   return COOP_OK;
@@ -3119,6 +3158,7 @@ coop_status coop_server_request_resources(coop_server *sv, int n_ctas, int timeo
     int n;
     uint32_t target;
     bool granted;
+    uint32_t run;
   };
   std::vector<Ask> asks;
   int from_idle = 0;
@@ -3165,8 +3205,9 @@ coop_status coop_server_request_resources(coop_server *sv, int n_ctas, int timeo
     for (size_t j = 0; j < idx.size(); ++j) {
       if (take[j] <= 0) continue;
       auto &sl = sv->slots[idx[j]];
-      Ask a{sl.ctx, take[j], 0u, false};
-      const coop_status st = post_kill(sl.ctx, a.n, &a.target, &a.granted);
+      Ask a{sl.ctx, take[j], 0u, false, 0u};
+      double lock_us = 0.0;
+      const coop_status st = post_kill(sl.ctx, a.n, &a.target, &a.granted, &lock_us, &a.run);
       if (st != COOP_OK) {
         if (worst == COOP_OK) worst = st;
         continue;
@@ -3180,7 +3221,8 @@ coop_status coop_server_request_resources(coop_server *sv, int n_ctas, int timeo
   const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(std::max(0, timeout_us));
   for (auto &a : asks) {
     int f = a.n;
-    const coop_status st = a.granted ? COOP_OK : wait_kill(a.ctx, a.target, a.n, timeout_us > 0, deadline, &f);
+    const coop_status st =
+        a.granted ? COOP_OK : wait_kill(a.ctx, a.target, a.n, a.run, timeout_us > 0, deadline, &f);
     got += f;
     if (st != COOP_OK && worst == COOP_OK) worst = st;
   }

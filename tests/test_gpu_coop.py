@@ -440,6 +440,7 @@ def test_request_log_records_every_request(ctx):
     assert [r["t_us"] for r in log] == sorted(r["t_us"] for r in log)
     for r, (n, got) in zip(log[1:], asks):
         assert r["n_ctas"] == n and r["granted"] == got == n and r["gather_us"] >= 0
+        assert 0 <= r["lock_us"] <= r["post_us"] <= r["gather_us"]
         for m in (r["active_at_post"], r["active_at_grant"]):
             assert m == 0 or 1 <= m <= N
     assert any(r["active_at_post"] > 0 for r in log[1:]), "no request landed during a traversal"
