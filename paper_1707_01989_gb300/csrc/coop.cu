@@ -430,32 +430,12 @@ __device__ __forceinline__ void select_interval(const Params &p, const Interval 
     cs.split[1] = 0xFFFFFFFFu;
     cs.take[0][0] = cs.take[0][1] = cs.take[1][0] = cs.take[1][1] = 0ull;
   }
-  const uint32_t step = GW * 32u;
-  // the entries of the first batch (kSelectBatch stripes per warp) and their current
-  // distances, loaded once: they are the histogram's sample and the first batch's input
-  uint32_t v[kSelectBatch], rs[kSelectBatch], deg[kSelectBatch], dd[kSelectBatch];
-  const auto load_batch = [&](uint32_t i0) {
-#pragma unroll
-    for (int k = 0; k < kSelectBatch; ++k) {
-      const uint32_t i = i0 + (uint32_t)k * step + lane;
-      v[k] = 0u;
-      rs[k] = 0u;
-      deg[k] = 0u;
-      if (i < F) {
-        v[k] = qv[i];
-        rs[k] = qs[i];
-        deg[k] = (i + 1u < F ? qo[i + 1u] : Etot) - qo[i];
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < kSelectBatch; ++k)
-      dd[k] = i0 + (uint32_t)k * step + lane < F ? (uint32_t)(__ldcg(p.ds + v[k]) >> 32) : 0u;
-  };
-  load_batch(first);
   workers_sync<NW>();
-#pragma unroll
-  for (int k = 0; k < kSelectBatch; ++k)
-    if (first + (uint32_t)k * step + lane < F) atomicAdd(&hs[dist_bucket(dd[k], iv.base)], deg[k]);
+  if (first + lane < F) {
+    const uint32_t i = first + lane;
+    const uint32_t deg = (i + 1u < F ? qo[i + 1u] : Etot) - qo[i];
+    atomicAdd(&hs[dist_bucket((uint32_t)(__ldcg(p.ds + qv[i]) >> 32), iv.base)], deg);
+  }
   workers_sync<NW>();
   if (warp == 0) {
     // the first bucket with cum * Etot >= B * total: lane l sums segment l (32 buckets),
@@ -491,17 +471,30 @@ __device__ __forceinline__ void select_interval(const Params &p, const Interval 
   const uint32_t bstar = cs.split[0];
   const uint32_t tag = sssp_tag(iv);
   uint32_t dmin = 0xFFFFFFFFu;
+  const uint32_t step = GW * 32u;
   // batches: the same count for every warp of the CTA (they meet at two CTA syncs each)
   const uint32_t nb = (F + kSelectBatch * step - 1u) / (kSelectBatch * step);
   for (uint32_t bi = 0, i0 = first; bi < nb; ++bi, i0 += kSelectBatch * step) {
     unsigned long long *take = cs.take[bi & 1u];
+    uint32_t v[kSelectBatch], rs[kSelectBatch], deg[kSelectBatch];
     bool near[kSelectBatch], far[kSelectBatch];
-    if (bi > 0u) load_batch(i0);
+#pragma unroll
+    for (int k = 0; k < kSelectBatch; ++k) {
+      const uint32_t i = i0 + (uint32_t)k * step + lane;
+      v[k] = 0u;
+      rs[k] = 0u;
+      deg[k] = 0u;
+      if (i < F) {
+        v[k] = qv[i];
+        rs[k] = qs[i];
+        deg[k] = (i + 1u < F ? qo[i + 1u] : Etot) - qo[i];
+      }
+    }
     uint32_t nN = 0u, nF = 0u, eN = 0u, eF = 0u;
 #pragma unroll
     for (int k = 0; k < kSelectBatch; ++k) {
       const bool valid = i0 + (uint32_t)k * step + lane < F;
-      const uint32_t d = dd[k];
+      const uint32_t d = valid ? (uint32_t)(__ldcg(p.ds + v[k]) >> 32) : 0u;
       near[k] = valid && dist_bucket(d, iv.base) <= bstar;
       far[k] = valid && !near[k];
       if (near[k]) dmin = min(dmin, d);
