@@ -1484,16 +1484,162 @@ __device__ void oct_scheduler(const OctParams &p, const volatile int32_t *worker
   }
 }
 
+// A cell's partition state in shared memory: octant counts, first places, scatter cursors,
+// and which octants become leaves.
+struct OctCell {
+  uint32_t hist[8], off[8], cur[8], leafmask;
+};
+// Cells below this many points are processed several at a time, one per warp group of a
+// CTA; larger ones by the whole CTA (they lie on the tree's critical path).
+constexpr uint32_t kOctSmall = 2048;
+__host__ __device__ constexpr int oct_groups(int nw) { return nw >= 24 ? 4 : nw >= 12 ? 2 : 1; }
+
+// One cell's work by T threads (gt = 0 .. T-1: a warp group, or the CTA's workers), whose
+// meeting point is sync(): a leaf's points copied to perm and its record written, or the
+// partition into octants (histogram, offsets, scatter; ballots aggregate each warp's
+// points per octant, shared-memory atomics per warp).  Children that will be leaves are
+// emitted here, not queued: their points go straight to perm during the scatter and their
+// records are written by thread 0, which also queues the other children on queue `slot`.
+template <typename Sync>
+__device__ __forceinline__ void oct_cell(const OctParams &p, const OctTask t, uint32_t gt, uint32_t T, OctCell &cs,
+                                         uint32_t slot, Sync sync) {
+  OctCtl *c = p.ctl;
+  const unsigned lane = threadIdx.x & 31u;
+  const uint32_t d = (uint32_t)(63 - __clzll((long long)t.code)) / 3u;
+  const uint32_t src = d & 1u, dst = src ^ 1u;
+  const bool leaf = t.count <= p.leaf_cap || d >= p.max_depth;
+  if (leaf) {
+    for (uint32_t i = gt; i < t.count; i += T) p.perm[t.begin + i] = __ldcg(p.bi[src] + t.begin + i);
+    if (gt == 0) {
+      const uint32_t li = atomicAdd(&c->leaves.v, 1u);
+      if (li < p.max_leaves) {
+        p.leaf_code[li] = t.code;
+        p.leaf_begin[li] = t.begin;
+        p.leaf_count[li] = t.count;
+      } else {
+        oct_error(p, ERR_OVERFLOW);
+      }
+    }
+  } else {
+    const uint32_t b = 20u - d;
+    if (gt < 8) cs.hist[gt] = 0u;
+    sync();
+    bool bad = false;
+    for (uint32_t i0 = 0; i0 < t.count; i0 += T) {
+      const uint32_t i = i0 + gt;
+      uint32_t o = 8u;
+      if (i < t.count) {
+        const uint32_t x = __ldcg(p.bx[src] + t.begin + i), y = __ldcg(p.by[src] + t.begin + i),
+                       z = __ldcg(p.bz[src] + t.begin + i);
+        if ((x | y | z) >> 21) bad = true;
+        o = octant(x, y, z, b);
+      }
+#pragma unroll
+      for (uint32_t k = 0; k < 8u; ++k) {
+        const unsigned m = __ballot_sync(kFull, o == k);
+        if (lane == 0 && m) atomicAdd(&cs.hist[k], (uint32_t)__popc(m));
+      }
+    }
+    if (bad) oct_error(p, ERR_GRAPH);
+    sync();
+    if (gt == 0) {
+      uint32_t acc = 0u, lm = 0u;
+      for (int k = 0; k < 8; ++k) {
+        cs.off[k] = acc;
+        cs.cur[k] = acc;
+        acc += cs.hist[k];
+        if (cs.hist[k] && (cs.hist[k] <= p.leaf_cap || d + 1u >= p.max_depth)) lm |= 1u << k;
+      }
+      cs.leafmask = lm;
+    }
+    sync();
+    const uint32_t leafmask = cs.leafmask;
+    const unsigned lt = lanemask_lt();
+    for (uint32_t i0 = 0; i0 < t.count; i0 += T) {
+      const uint32_t i = i0 + gt;
+      uint32_t o = 8u, x = 0u, y = 0u, z = 0u, id = 0u;
+      if (i < t.count) {
+        x = __ldcg(p.bx[src] + t.begin + i);
+        y = __ldcg(p.by[src] + t.begin + i);
+        z = __ldcg(p.bz[src] + t.begin + i);
+        id = __ldcg(p.bi[src] + t.begin + i);
+        o = octant(x, y, z, b) & 7u;
+      }
+      uint32_t pos = 0u;
+#pragma unroll
+      for (uint32_t k = 0; k < 8u; ++k) {
+        const unsigned m = __ballot_sync(kFull, o == k && i < t.count);
+        if (m) {
+          const unsigned first = (unsigned)__ffs(m) - 1u;
+          uint32_t base = 0u;
+          if (lane == first) base = atomicAdd(&cs.cur[k], (uint32_t)__popc(m));
+          base = __shfl_sync(kFull, base, first);
+          if (o == k && i < t.count) pos = base + (uint32_t)__popc(m & lt);
+        }
+      }
+      if (i < t.count) {
+        const uint32_t at = t.begin + pos;
+        if ((leafmask >> o) & 1u) {
+          p.perm[at] = id;
+        } else {
+          p.bx[dst][at] = x;
+          p.by[dst][at] = y;
+          p.bz[dst][at] = z;
+          p.bi[dst][at] = id;
+        }
+      }
+    }
+  }
+  __threadfence();  // these threads' writes before the tasks that will read them
+  sync();
+  if (gt == 0) {
+    OctTask ch[8];
+    uint32_t nc = 0u;
+    if (!leaf) {
+      const uint32_t lm = cs.leafmask;
+      const uint32_t nleaf = (uint32_t)__popc(lm);
+      if (nleaf) {
+        const uint32_t li = atomicAdd(&c->leaves.v, nleaf);
+        uint32_t j = 0u;
+        for (uint32_t k = 0; k < 8u; ++k) {
+          if (!((lm >> k) & 1u)) continue;
+          if (li + j < p.max_leaves) {
+            p.leaf_code[li + j] = (t.code << 3) | k;
+            p.leaf_begin[li + j] = t.begin + cs.off[k];
+            p.leaf_count[li + j] = cs.hist[k];
+          } else {
+            oct_error(p, ERR_OVERFLOW);
+          }
+          ++j;
+        }
+      }
+      for (uint32_t k = 0; k < 8u; ++k)
+        if (cs.hist[k] && !((lm >> k) & 1u)) ch[nc++] = OctTask{t.begin + cs.off[k], cs.hist[k], (t.code << 3) | k};
+      atomicAdd(&c->moved, (unsigned long long)t.count);
+    }
+    bool ok = true;
+    if (nc) ok = oct_push(p, slot, ch, nc);
+    atomicAdd(&c->tasks, 1ull);
+    if (ok) {
+      // this task is done and nc are new: the run ends when none is outstanding
+      const uint32_t prev = atomicAdd(&c->outstanding.v, nc - 1u);
+      if (prev + nc - 1u == 0u) st_release(&c->done.v, 1u);
+    }
+  }
+}
+
 template <int NW>
 __global__ void __launch_bounds__((NW + 1) * 32, 1) coop_octree_kernel(const __grid_constant__ OctParams p, int join) {
   extern __shared__ __align__(16) unsigned char oct_reserve[];  // SM-exclusivity reservation only
   (void)oct_reserve;
-  __shared__ OctTask s_task;
+  constexpr int G = oct_groups(NW);
+  __shared__ OctTask s_task[G];
+  __shared__ OctCell s_cell[G];
   __shared__ int32_t s_state, s_workers_left;
-  __shared__ uint32_t s_slot, s_hist[8], s_off[8], s_cur[8], s_leafmask;
+  __shared__ uint32_t s_slot, s_ntask;
   OctCtl *c = p.ctl;
   const bool master = !join && blockIdx.x == 0;
-  const unsigned tid = threadIdx.x, lane = tid & 31u;
+  const unsigned tid = threadIdx.x;
   constexpr uint32_t T = NW * 32;
   if (tid == 0) {
     s_slot = atomicAdd(&c->slots.v, 1u) % kOctQueues;
@@ -1504,6 +1650,13 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) coop_octree_kernel(const __g
     if (master && p.coop && tid == T) oct_scheduler<NW>(p, &s_workers_left);
     return;
   }
+  // warp group g: warps [g * NW / G, (g + 1) * NW / G), named barrier 2 + g
+  const uint32_t warp = tid >> 5;
+  uint32_t g = 0;
+  while (g + 1 < (uint32_t)G && warp >= (g + 1) * NW / G) ++g;
+  const uint32_t w0 = g * NW / G, Tg = ((g + 1) * NW / G - w0) * 32u;
+  const auto cta_sync = [] { workers_sync<NW>(); };
+  const auto group_sync = [g, Tg] { asm volatile("bar.sync %0, %1;" ::"r"(2u + g), "r"(Tg) : "memory"); };
   uint64_t idle0 = 0;
   for (;;) {
     if (tid == 0) {
@@ -1535,7 +1688,20 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) coop_octree_kernel(const __g
           }
         }
         if (st == 1) {
-          s_task = t;
+          s_task[0] = t;
+          uint32_t n = 1u;
+          // a small cell: take more small ones from this CTA's own queue, one per group
+          // (a large one popped meanwhile goes back, to be taken whole next time)
+          while (G > 1 && t.count < kOctSmall && n < (uint32_t)G) {
+            OctTask u;
+            if (!oct_pop(p, s_slot, true, u)) break;
+            if (u.count >= kOctSmall) {
+              oct_push(p, s_slot, &u, 1u);
+              break;
+            }
+            s_task[n++] = u;
+          }
+          s_ntask = n;
           idle0 = 0;
         } else if (ld_acquire(&c->outstanding.v) == 0u || ld_relaxed(&c->done.v) != 0u ||
                    ld_relaxed(&c->err.v) != 0u) {
@@ -1563,132 +1729,9 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) coop_octree_kernel(const __g
       break;
     }
     if (st == 1) {
-      const OctTask t = s_task;
-      const uint32_t d = (uint32_t)(63 - __clzll((long long)t.code)) / 3u;
-      const uint32_t src = d & 1u, dst = src ^ 1u;
-      if (t.count <= p.leaf_cap || d >= p.max_depth) {
-        for (uint32_t i = tid; i < t.count; i += T) p.perm[t.begin + i] = __ldcg(p.bi[src] + t.begin + i);
-        if (tid == 0) {
-          const uint32_t li = atomicAdd(&c->leaves.v, 1u);
-          if (li < p.max_leaves) {
-            p.leaf_code[li] = t.code;
-            p.leaf_begin[li] = t.begin;
-            p.leaf_count[li] = t.count;
-          } else {
-            oct_error(p, ERR_OVERFLOW);
-          }
-          s_hist[0] = 0xFFFFFFFFu;  // marks a leaf: no children
-        }
-      } else {
-        // partition by the octant at this depth: histogram, offsets, scatter (ballots
-        // aggregate each warp's points per octant; shared-memory atomics per warp)
-        const uint32_t b = 20u - d;
-        if (tid < 8) s_hist[tid] = 0u;
-        workers_sync<NW>();
-        bool bad = false;
-        for (uint32_t i0 = 0; i0 < t.count; i0 += T) {
-          const uint32_t i = i0 + tid;
-          uint32_t o = 8u;
-          if (i < t.count) {
-            const uint32_t x = __ldcg(p.bx[src] + t.begin + i), y = __ldcg(p.by[src] + t.begin + i),
-                           z = __ldcg(p.bz[src] + t.begin + i);
-            if ((x | y | z) >> 21) bad = true;
-            o = octant(x, y, z, b);
-          }
-#pragma unroll
-          for (uint32_t k = 0; k < 8u; ++k) {
-            const unsigned m = __ballot_sync(kFull, o == k);
-            if (lane == 0 && m) atomicAdd(&s_hist[k], (uint32_t)__popc(m));
-          }
-        }
-        if (bad) oct_error(p, ERR_GRAPH);
-        workers_sync<NW>();
-        if (tid == 0) {
-          // children that will be leaves are emitted here, not queued: their points go
-          // straight to perm during the scatter and their records are written below
-          uint32_t acc = 0u, lm = 0u;
-          for (int k = 0; k < 8; ++k) {
-            s_off[k] = acc;
-            s_cur[k] = acc;
-            acc += s_hist[k];
-            if (s_hist[k] && (s_hist[k] <= p.leaf_cap || d + 1u >= p.max_depth)) lm |= 1u << k;
-          }
-          s_leafmask = lm;
-        }
-        workers_sync<NW>();
-        const uint32_t leafmask = s_leafmask;
-        const unsigned lt = lanemask_lt();
-        for (uint32_t i0 = 0; i0 < t.count; i0 += T) {
-          const uint32_t i = i0 + tid;
-          uint32_t o = 8u, x = 0u, y = 0u, z = 0u, id = 0u;
-          if (i < t.count) {
-            x = __ldcg(p.bx[src] + t.begin + i);
-            y = __ldcg(p.by[src] + t.begin + i);
-            z = __ldcg(p.bz[src] + t.begin + i);
-            id = __ldcg(p.bi[src] + t.begin + i);
-            o = octant(x, y, z, b) & 7u;
-          }
-          uint32_t pos = 0u;
-#pragma unroll
-          for (uint32_t k = 0; k < 8u; ++k) {
-            const unsigned m = __ballot_sync(kFull, o == k && i < t.count);
-            if (m) {
-              const unsigned first = (unsigned)__ffs(m) - 1u;
-              uint32_t base = 0u;
-              if (lane == first) base = atomicAdd(&s_cur[k], (uint32_t)__popc(m));
-              base = __shfl_sync(kFull, base, first);
-              if (o == k && i < t.count) pos = base + (uint32_t)__popc(m & lt);
-            }
-          }
-          if (i < t.count) {
-            const uint32_t at = t.begin + pos;
-            if ((leafmask >> o) & 1u) {
-              p.perm[at] = id;
-            } else {
-              p.bx[dst][at] = x;
-              p.by[dst][at] = y;
-              p.bz[dst][at] = z;
-              p.bi[dst][at] = id;
-            }
-          }
-        }
-      }
-      __threadfence();  // this CTA's writes before the tasks that will read them
-      workers_sync<NW>();
-      if (tid == 0) {
-        OctTask ch[8];
-        uint32_t nc = 0u;
-        if (s_hist[0] != 0xFFFFFFFFu) {
-          const uint32_t lm = s_leafmask;
-          const uint32_t nleaf = (uint32_t)__popc(lm);
-          if (nleaf) {
-            const uint32_t li = atomicAdd(&c->leaves.v, nleaf);
-            uint32_t j = 0u;
-            for (uint32_t k = 0; k < 8u; ++k) {
-              if (!((lm >> k) & 1u)) continue;
-              if (li + j < p.max_leaves) {
-                p.leaf_code[li + j] = (t.code << 3) | k;
-                p.leaf_begin[li + j] = t.begin + s_off[k];
-                p.leaf_count[li + j] = s_hist[k];
-              } else {
-                oct_error(p, ERR_OVERFLOW);
-              }
-              ++j;
-            }
-          }
-          for (uint32_t k = 0; k < 8u; ++k)
-            if (s_hist[k] && !((lm >> k) & 1u)) ch[nc++] = OctTask{t.begin + s_off[k], s_hist[k], (t.code << 3) | k};
-          atomicAdd(&c->moved, (unsigned long long)t.count);
-        }
-        bool ok = true;
-        if (nc) ok = oct_push(p, s_slot, ch, nc);
-        atomicAdd(&c->tasks, 1ull);
-        if (ok) {
-          // this task is done and nc are new: the run ends when none is outstanding
-          const uint32_t prev = atomicAdd(&c->outstanding.v, nc - 1u);
-          if (prev + nc - 1u == 0u) st_release(&c->done.v, 1u);
-        }
-      }
+      const uint32_t nt = s_ntask;
+      if (nt == 1u) oct_cell(p, s_task[0], tid, T, s_cell[0], s_slot, cta_sync);
+      else if (g < nt) oct_cell(p, s_task[g], tid - w0 * 32u, Tg, s_cell[g], s_slot, group_sync);
     }
     workers_sync<NW>();  // s_state and s_task are rewritten only after every worker read them
   }
