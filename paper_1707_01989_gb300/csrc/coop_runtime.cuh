@@ -762,7 +762,12 @@ __device__ __forceinline__ bool resizing_barrier(const Params &p, CtaShared &cs)
       __threadfence_block();
       cs.iv = nxt;
     }
-    if (leave) atomicAdd(&c->surrendered, 1u);
+    if (leave) {
+      // the host sees the CTA go at once; the scheduler warp republishes the count in order
+      // (two leavers' stores may reach the host out of order)
+      const uint32_t v = atomicAdd(&c->surrendered, 1u) + 1u;
+      if (p.coop) st_sys(&p.mbox->freed, p.kill_base + v);
+    }
     cs.ok = ok ? 1 : 0;
     cs.leave = leave ? 1 : 0;
   }
