@@ -79,14 +79,18 @@ def peaks():
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region: the
     sampler is running (its first sample in) before the region starts, samples every
-    20 ms, and only samples taken from the region's start on are summarised."""
+    `every_ms` (20 ms by default, for timed regions of tens of milliseconds), and only
+    samples taken from the region's start on are summarised.  Latency measurements that
+    run for seconds sample every 200 ms: each query takes the driver's locks, which a
+    CUDA call made meanwhile (a launch, a synchronise) waits for."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device_index: int):
+    def __init__(self, device_index: int, every_ms: int = 20):
         self.dev = device_index
+        self.every_ms = int(every_ms)
         self.proc = None
         self.lines = []  # (host time, line)
         self.t0 = 0.0
@@ -95,7 +99,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.every_ms)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
             t_wait = time.perf_counter()
@@ -112,7 +116,7 @@ class ClockSampler:
 
     def __exit__(self, *a):
         if self.proc:
-            time.sleep(0.03)  # one more sample after the region
+            time.sleep(min(0.25, 1.5 * self.every_ms / 1e3))  # one more sample after the region
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -1305,7 +1309,7 @@ def secondary(coop, ctx, dev, stream, flush, args, head):
         stream.synchronize()
         vr, es = reached_work(g, ref >= 0)
         B = 4 * g.num_vertices + 20 * vr + 8 * es
-        with ClockSampler(dev.index or 0) as ck:
+        with ClockSampler(dev.index or 0, every_ms=200) as ck:
             res = corunner(coop, ctx, dev, csr, src, lv, stream, work=(es, B, hbm))
         res["clocks"] = ck.summary()
         res["bit_exact"] = bool(np.array_equal(lv.cpu().numpy(), ref))
@@ -1333,10 +1337,10 @@ def secondary(coop, ctx, dev, stream, flush, args, head):
                               "baseline_kernel_us": round(kusb, 2), "coop_overhead": round(kus / kusb, 4)}}
         res["bfs_rmat22_schedules"] = random_schedules(coop, ctx, csr, src, lv, lvh, stream, es)
         # each with the clocks seen while it ran: a throttling episode shows up beside it
-        with ClockSampler(dev.index or 0) as ck:
+        with ClockSampler(dev.index or 0, every_ms=200) as ck:
             res["corunner"] = corunner(coop, ctx, dev, csr, src, lv, stream, work=(es, B, hbm))
         res["corunner"]["clocks"] = ck.summary()
-        with ClockSampler(dev.index or 0) as ck:
+        with ClockSampler(dev.index or 0, every_ms=200) as ck:
             res["table3"] = table3(coop, ctx, dev, stream, csr, src, lv, lvh)
         res["table3"]["clocks"] = ck.summary()
         return res

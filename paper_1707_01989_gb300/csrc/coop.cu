@@ -933,8 +933,10 @@ __device__ __forceinline__ void scheduler_warp(const Params &p, const volatile i
   Ctl *c = p.ctl;
   uint32_t forks_seen = p.fork_base, freed_seen = 0u, host_req_seen = 0u;
   for (;;) {
-    // both host counters in one system-scope load: (fork_req << 32) | kill_req
+    // both host counters in one system-scope load: (fork_req << 32) | kill_req; and the
+    // count of freed CTAs the host sees (issued together: two independent round trips)
     const uint64_t req = ld_sys64(&p.mbox->kill_req);
+    const uint32_t host_freed = ld_sys(&p.mbox->freed);
     const uint32_t r = (uint32_t)req, f = (uint32_t)(req >> 32);
     if (p.kill_mode == KILL_SIMPLE) {
       // the regular barrier: arriving CTAs compare this with the kills already decided
@@ -963,8 +965,13 @@ __device__ __forceinline__ void scheduler_warp(const Params &p, const volatile i
         }
       }
     }
+    // A CTA that leaves on a host request publishes the count itself (the host sees it at
+    // once), but two such stores from different SMs can reach host memory in either
+    // order, the lower count last; the host would then wait for the traversal's end.  So
+    // the count is rewritten here whenever it changed or the host's copy differs from it
+    // (until the traversal is over: the host then grants what is left itself).
     const uint32_t sur = ld_relaxed(&c->surrendered);
-    if (sur != freed_seen) {
+    if ((sur != freed_seen || host_freed != p.kill_base + sur) && ld_relaxed(&c->done) == 0u) {
       st_sys(&p.mbox->freed, p.kill_base + sur);
       freed_seen = sur;
     }
@@ -2033,19 +2040,28 @@ coop_status post_kill(coop_ctx *c, int n, uint32_t *target, bool *granted, doubl
 
 // Waits until the device has freed the CTAs of a posted request (or the traversal ended,
 // which grants the rest: seen first as the run's id in the mailbox, then as its
-// completion), or until `deadline`; *got = the request's CTAs freed so far.
+// completion), or until `deadline`; *got = the request's CTAs freed so far.  While the
+// traversal runs the loop reads host memory only: the completion event is queried (a
+// CUDA call, which can wait behind another process's driver queries) only once the run
+// has published its end, and otherwise once a millisecond, in case it never does.
 coop_status wait_kill(coop_ctx *c, uint32_t target, int n, uint32_t run, bool bounded,
                       std::chrono::steady_clock::time_point deadline, int *got) {
   const auto t0 = std::chrono::steady_clock::now();
+  auto fallback = t0 + std::chrono::milliseconds(1);
   for (uint32_t spin = 0;; ++spin) {
     const uint32_t f = load_acquire(&c->mbox->freed);
     *got = std::max(0, std::min(n, (int)(f - (target - (uint32_t)n))));
     if ((int32_t)(f - target) >= 0) break;
-    if ((spin & 63u) == 0u || load_acquire(&c->mbox->run_done) == run) {
-      std::lock_guard<std::mutex> lk(c->mu);
-      if (!busy_locked(c)) {
-        finalize_locked(c);
-        break;
+    const bool ended = load_acquire(&c->mbox->run_done) == run;
+    if (ended || (spin & 63u) == 0u) {
+      const auto now = std::chrono::steady_clock::now();
+      if (ended || now >= fallback) {
+        fallback = now + std::chrono::milliseconds(1);
+        std::lock_guard<std::mutex> lk(c->mu);
+        if (!busy_locked(c)) {
+          finalize_locked(c);
+          break;
+        }
       }
     }
     if (bounded && std::chrono::steady_clock::now() > deadline) return COOP_ETIMEOUT;
