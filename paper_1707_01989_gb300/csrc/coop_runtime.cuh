@@ -934,7 +934,7 @@ __device__ __forceinline__ void master_enter(const Params &p, CtaShared &cs) {
   iv.done = (count == 0u || ld_relaxed(&c->err) != 0u) ? 1u : 0u;
   iv.epoch = 1u;
   iv.doom = (uint32_t)(1 + k);
-  iv.precheck = precheck_hint(edges);
+  iv.precheck = 0u;  // only the source is reached yet: every target is a candidate
   iv.base = 0u;
   iv.sssp = sssp_word(0u, 0u, 0u);  // SSSP round 0 expands the source's pending queue whole
   iv.cont = 0u;
