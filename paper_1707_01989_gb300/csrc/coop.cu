@@ -1390,6 +1390,7 @@ struct OctParams {
   uint64_t timeout_ns;
   uint32_t pre;  // 1: the top kPreDepth levels are partitioned grid-wide before the work stealing
   uint32_t *cell_count, *cell_begin, *cell_cursor, *cell_leaf;  // kPreCells each
+  uint32_t run;  // the context's run id, published to the host when the build is over
 };
 
 // Grid-wide partition of the top levels: the first kPreDepth levels of a large tree would
@@ -1897,6 +1898,10 @@ __global__ void __launch_bounds__(512) coop_octree_pre_scatter(const __grid_cons
 
 __global__ void coop_octree_finish(const __grid_constant__ OctParams p) {
   *p.n_leaves = (int32_t)min(p.ctl->leaves.v, p.max_leaves);
+  // the build is over: a host request still waiting is granted from the remaining CTAs
+  __threadfence_system();
+  st_sys(&p.mbox->run_done, p.run);
+  __threadfence_system();
 }
 
 const void *octree_fn(int nw) {
@@ -2007,12 +2012,18 @@ bool finished_locked(coop_ctx *c) {
 // A traversal holds CTAs that a request must wait for.
 bool busy_locked(coop_ctx *c) { return !finished_locked(c) && running(c); }
 
+// The same from host memory alone (no CUDA call, which can wait behind another thread's
+// driver calls): a launched run that has not published its end counts as running.  A
+// run that ended without publishing it (an error) is found by the request wait's
+// periodic busy_locked.
+bool busy_nowait_locked(coop_ctx *c) { return !finished_locked(c) && (c->launching || c->launched); }
+
 // Fold the CTAs the device has surrendered into the host's books (always), and once no
 // traversal holds CTAs grant every still-outstanding request at once.
-void finalize_locked(coop_ctx *c) {
+void finalize_locked(coop_ctx *c, bool nowait = false) {
   const uint32_t f = load_acquire(&c->mbox->freed);
   if ((int32_t)(f - c->served) > 0) c->served = f;
-  if (busy_locked(c)) return;
+  if (nowait ? busy_nowait_locked(c) : busy_locked(c)) return;
   (void)cudaGetLastError();
   if ((int32_t)(c->kill_req - c->served) > 0) c->served = c->kill_req;  // idle grant
   store_release(&c->mbox->freed, c->served);
@@ -2026,15 +2037,15 @@ coop_status post_kill(coop_ctx *c, int n, uint32_t *target, bool *granted, doubl
   const auto t0 = std::chrono::steady_clock::now();
   std::lock_guard<std::mutex> lk(c->mu);
   *lock_us = std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count();
-  finalize_locked(c);
+  finalize_locked(c, true);
   const int outstanding = (int)(c->kill_req - c->returned);
   if (outstanding + n > c->N - 1) return COOP_EINVAL;
   c->kill_req += (uint32_t)n;
   *target = c->kill_req;
   store_release(&c->mbox->kill_req, c->kill_req);
   *run = c->cur.run;
-  *granted = !busy_locked(c);
-  if (*granted) finalize_locked(c);
+  *granted = !busy_nowait_locked(c);
+  if (*granted) finalize_locked(c, true);
   return COOP_OK;
 }
 
@@ -3525,6 +3536,10 @@ coop_status coop_octree(coop_ctx *c, const uint32_t *d_x, const uint32_t *d_y, c
     p.n_leaves = d_n_leaves;
     p.max_leaves = (uint32_t)max_leaves;
     p.mbox = c->mbox_d;
+    // a run id of its own: a request posted while the octree is built waits for its CTAs
+    // (or for the build's end, which the finish kernel publishes)
+    p.run = ++c->run;
+    c->cur.run = p.run;
     const int held = (int)(c->served - c->returned);
     p.launched = (uint32_t)std::max(1, c->N - held);
     p.kill_base = c->served;
