@@ -54,8 +54,8 @@ WORKLOADS = {
 # workload, from the ncu captures summarised in profiles/; an entry is used only while
 # the kernel sources still have the digest it was taken on (otherwise null).
 TRAFFIC = {
-    "rmat22-bfs": {"sources_sha": "6504f82ec53cc4f7", "bytes": 391175168},
-    "rmat20-sssp": {"sources_sha": "6504f82ec53cc4f7", "bytes": 200252416},
+    "rmat22-bfs": {"sources_sha": "e40980aa03f47f9a", "bytes": 391103744},
+    "rmat20-sssp": {"sources_sha": "e40980aa03f47f9a", "bytes": 199846144},
 }
 
 
