@@ -120,6 +120,44 @@ def test_octree_under_host_requests(ctx):
     coop.coop_sync(ctx)
 
 
+def test_request_during_a_build_waits_for_its_ctas(ctx):
+    """A request posted while an octree is being built is served by the build's CTAs
+    leaving at the head of its loop, not granted at once: a build has a run id of its own,
+    which the host sees published only when the build is over.  (A request granted at
+    once is recorded with M = 0 and no wait; the traversal run first leaves a published
+    M in the mailbox, which a request that waits records.)"""
+    import torch
+    from gpu_util import DevGraph, run_bfs
+    run_bfs(ctx, DevGraph(gg.grid(64, 64)), 0)
+    N = coop.coop_query(ctx)["max_ctas"]
+    pts = gg.points(1 << 20, 91, "clustered")
+    exp_codes = ot.leaf_code_of_points(*pts, 16, 21)
+    x, y, z = (torch.from_numpy(a.view(np.int32)).cuda() for a in pts)
+    n = len(pts[0])
+    code = torch.empty(n, dtype=torch.int64, device="cuda")
+    begin = torch.empty(n, dtype=torch.int32, device="cuda")
+    count = torch.empty(n, dtype=torch.int32, device="cuda")
+    perm = torch.empty(n, dtype=torch.int32, device="cuda")
+    nl = torch.empty(1, dtype=torch.int32, device="cuda")
+    coop.coop_get_request_log(ctx, clear=True)
+    coop.coop_octree(ctx, x, y, z, 16, 21, code, begin, count, perm, nl)  # returns once launched
+    got = coop.coop_request_resources(ctx, N // 2, timeout_us=2_000_000)
+    coop.coop_release(ctx, got)
+    torch.cuda.synchronize()
+    rec = coop.coop_get_request_log(ctx, clear=True)[-1]
+    assert got == N // 2
+    assert rec["active_at_post"] > 0, rec  # not granted at once
+    assert rec["gather_us"] - rec["post_us"] > 1.0, rec
+    k = int(nl.item())
+    codes = code[:k].cpu().numpy().view(np.uint64)
+    b, c, p = begin[:k].cpu().numpy(), count[:k].cpu().numpy(), perm.cpu().numpy()
+    leaf_of = np.zeros(n, dtype=np.uint64)
+    for cd, bb, cc in zip(codes, b, c):
+        leaf_of[p[bb:bb + cc]] = cd
+    assert np.array_equal(leaf_of, exp_codes)
+    coop.coop_sync(ctx)
+
+
 def test_octree_errors(ctx):
     pts = gg.points(2000, 3, "uniform")
     bad = (pts[0].copy(), pts[1], pts[2])
