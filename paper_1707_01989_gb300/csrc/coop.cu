@@ -358,12 +358,47 @@ __device__ __forceinline__ void issue_groups(const Params &p, const uint32_t *qo
     cp_async_commit();
     return;
   }
+  // One slide to c: lane 0 then holds the entry containing c.  When the window's 32
+  // entries reach the end of the iteration (rows of 4 or more edges on average: nearly
+  // every iteration of a wide R-MAT level that spans several rows), every group's source
+  // entries are found in the window as it is -- the entry containing the group's first
+  // edge is the last lane whose entry starts at or before it -- and the next iteration's
+  // slide drops at most 32 entries.  Otherwise the window slides group by group.
+  slide<MODE>(p, qo, qs, qv, F, Etot, c, w, wb, lane);
+  if (__shfl_sync(kFull, w.end, 31) >= min(c + 32u * kUnroll, E1)) {
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint32_t cu = c + 32u * (uint32_t)u;
+      if (cu >= E1) break;  // warp-uniform
+      const unsigned k = 31u - (unsigned)__clz(__ballot_sync(kFull, w.off <= cu));  // lane 0's entry qualifies
+      // entries starting strictly inside (cu, cu + 32) -> source entry of each lane's edge
+      const uint32_t rel = w.off - cu;
+      const unsigned bit = (rel - 1u < 31u) ? (1u << rel) : 0u;
+      const unsigned bits = __reduce_or_sync(kFull, bit);
+      const unsigned idx = k + (unsigned)__popc(bits & lm_le);
+      const uint32_t s0 = __shfl_sync(kFull, w.start, idx);
+      const uint32_t o0 = __shfl_sync(kFull, w.off, idx);
+      uint32_t du = 0u;
+      if (MODE == MODE_SSSP) du = __shfl_sync(kFull, w.du, idx);
+      const uint32_t e = cu + lane;
+      if (e < E1) {
+        const uint32_t pos = s0 + (e - o0);
+        cp_async4(&pf.col[sb][u][lane], p.col + pos);
+        if constexpr (MODE == MODE_SSSP) {
+          cp_async4(&pf.w[sb][u][lane], p.w + pos);
+          pf.du[sb][u][lane] = du;
+        }
+      }
+    }
+    cp_async_commit();
+    return;
+  }
 #pragma unroll
   for (int u = 0; u < kUnroll; ++u) {
     const uint32_t cu = c + 32u * (uint32_t)u;
     if (cu >= E1) break;  // warp-uniform
     // every entry holds at least one edge, so one slide covers a 32-edge step
-    slide<MODE>(p, qo, qs, qv, F, Etot, cu, w, wb, lane);
+    if (u > 0) slide<MODE>(p, qo, qs, qv, F, Etot, cu, w, wb, lane);
     // entries starting strictly inside [cu, cu+32) -> source entry of each lane's edge
     const uint32_t rel = w.off - cu;
     const unsigned bit = (lane != 0u && rel < 32u) ? (1u << rel) : 0u;

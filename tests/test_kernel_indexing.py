@@ -10,7 +10,8 @@ that arithmetic in numpy (one vector = one warp) over random frontiers and check
 every lane reads column start[u] + (e - off[u]) of the entry u that owns edge e, i.e.
 that no column read can leave its row, and that every edge is expanded exactly once --
 including the fast path that skips the per-group arithmetic when lane 0's entry covers a
-whole 128-edge iteration.
+whole 128-edge iteration, and the path that maps all four groups of an iteration from
+one window position when its 32 entries reach the iteration's end.
 It runs before any GPU code does.
 """
 import numpy as np
@@ -143,6 +144,31 @@ def emulate_warp(qo, qs, F, Etot, E0, E1, wb=None):
             s0, o0 = win[0][2], win[0][0]
             for e in range(it, min(it + 128, E1)):
                 out.append((e, (s0 + ((e - o0) & FULL)) & FULL))
+            continue
+        # one slide to the iteration's first edge; if the window then reaches the
+        # iteration's end, the groups map their lanes without sliding again
+        ended = ballot(np.array([w[1] <= it for w in win]))
+        if ended:
+            n = popc(ended)
+            wb += n
+            win = [win[(l + n) & 31] if l + n < 32 else load(qo, qs, F, Etot, wb + l) for l in range(32)]
+        if win[31][1] >= min(it + 128, E1):
+            for c in range(it, min(it + 128, E1), 32):
+                km = ballot(np.array([w[0] <= c for w in win]))
+                k = km.bit_length() - 1
+                assert k >= 0
+                bits = 0
+                for l in range(32):
+                    rel = (win[l][0] - c) & FULL
+                    if ((rel - 1) & FULL) < 31:
+                        bits |= 1 << rel
+                for l in range(32):
+                    idx = k + popc(bits & ((2 << l) - 1))
+                    e = c + l
+                    if e < E1:
+                        assert idx < 32
+                        s0, o0 = win[idx][2], win[idx][0]
+                        out.append((e, (s0 + ((e - o0) & FULL)) & FULL))
             continue
         for c in range(it, min(it + 128, E1), 32):
             ended = ballot(np.array([w[1] <= c for w in win]))
