@@ -54,8 +54,8 @@ WORKLOADS = {
 # workload, from the ncu captures summarised in profiles/; an entry is used only while
 # the kernel sources still have the digest it was taken on (otherwise null).
 TRAFFIC = {
-    "rmat22-bfs": {"sources_sha": "e40980aa03f47f9a", "bytes": 391103744},
-    "rmat20-sssp": {"sources_sha": "e40980aa03f47f9a", "bytes": 199846144},
+    "rmat22-bfs": {"sources_sha": "1f6f5f36c732ece4", "bytes": 391598592},
+    "rmat20-sssp": {"sources_sha": "1f6f5f36c732ece4", "bytes": 201957120},
 }
 
 
